@@ -1,0 +1,247 @@
+"""numpy front end of the FP64 C oracle (``vapr_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product path.
+
+Every function converts its float32 inputs once and hands them to the C
+code, which computes in double precision.  See ``vapr_oracle.h`` for the
+readings of the paper each function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vapr_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+
+# Special-value classes, mirroring the OR_* constants of vapr_oracle.h.
+IEEE = 1
+FN = 2
+SAT = 4
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (OpenMP when available)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(os.path.join(_HERE, "vapr_oracle.h")))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+            "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        i32, i64, u32, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+        sig = {
+            "or_exmy_encode": (u32, [ctypes.c_float, i32, i32, u32]),
+            "or_exmy_decode": (dbl, [u32, i32, i32, u32]),
+            "or_exmy_max_finite": (dbl, [i32, i32, u32]),
+            "or_exmy_encode_batch": (None, [P, i64, i32, i32, u32, P]),
+            "or_exmy_encode_bits_range": (None, [u32, i64, i32, i32, u32, P]),
+            "or_exmy_decode_batch": (None, [P, i64, i32, i32, u32, P]),
+            "or_pack_rows": (None, [P, i64, i64, i32, P, i64]),
+            "or_unpack_rows": (None, [P, i64, i64, i32, i64, P]),
+            "or_fk": (None, [i32, P, i32, P, P, P, i64, P, P]),
+            "or_box_sdf_batch": (None, [P, P, P, i64, P, P]),
+            "or_collision": (None, [i32, P, i32, P, i32, P, P, dbl, dbl, dbl,
+                                    dbl, P, i64, P, P, P, P, dbl]),
+            "or_backward": (None, [i32, P, i32, P, P, P, P, P, i64, P]),
+            "or_scene_sdf": (None, [i32, P, P, P, i64, P]),
+            "or_num_threads": (i32, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+# ----------------------------------------------------------------- formats
+def default_flags(E: int, M: int) -> int:
+    """Special-value class of each format (reading; Sec. IV-A is silent):
+    float32/bfloat16/half are IEEE with overflow to Inf; E5M2 is IEEE with
+    saturation; E4M3 is the OCP "fn" variant (no Inf, one NaN, saturation);
+    every other ExMy format is finite-only and saturates."""
+    if (E, M) in ((8, 23), (8, 7), (5, 10)):
+        return IEEE
+    if (E, M) == (5, 2):
+        return IEEE | SAT
+    if (E, M) == (4, 3):
+        return FN | SAT
+    if E == 8:
+        # 8 exponent bits: Inf/NaN reserved as in bfloat16, saturating
+        return IEEE | SAT
+    return SAT
+
+
+def encode(x, E: int, M: int, flags: int | None = None) -> np.ndarray:
+    flags = default_flags(E, M) if flags is None else flags
+    x = _c(x, np.float32)
+    out = np.empty(x.shape, np.uint32)
+    _load().or_exmy_encode_batch(_p(x), x.size, E, M, flags, _p(out))
+    return out
+
+
+def encode_bits_range(start: int, count: int, E: int, M: int,
+                      flags: int | None = None) -> np.ndarray:
+    flags = default_flags(E, M) if flags is None else flags
+    out = np.empty(count, np.uint32)
+    _load().or_exmy_encode_bits_range(start, count, E, M, flags, _p(out))
+    return out
+
+
+def decode(codes, E: int, M: int, flags: int | None = None) -> np.ndarray:
+    flags = default_flags(E, M) if flags is None else flags
+    codes = _c(codes, np.uint32)
+    out = np.empty(codes.shape, np.float64)
+    _load().or_exmy_decode_batch(_p(codes), codes.size, E, M, flags, _p(out))
+    return out
+
+
+def quantize(x, E: int, M: int, flags: int | None = None) -> np.ndarray:
+    """float32 -> format -> exact value (float64)."""
+    return decode(encode(x, E, M, flags), E, M, flags)
+
+
+def max_finite(E: int, M: int, flags: int | None = None) -> float:
+    flags = default_flags(E, M) if flags is None else flags
+    return float(_load().or_exmy_max_finite(E, M, flags))
+
+
+def packed_row_bytes(row_len: int, bits: int) -> int:
+    """Bytes of one packed row: floor(32/bits) codes per 32-bit word, the
+    row padded to a multiple of 16 bytes."""
+    k = 32 // bits
+    words = -(-row_len // k)
+    return -(-4 * words // 16) * 16
+
+
+def pack_rows(codes, bits: int, row_stride: int | None = None) -> np.ndarray:
+    codes = _c(codes, np.uint32)
+    rows, row_len = codes.shape
+    stride = packed_row_bytes(row_len, bits) if row_stride is None else row_stride
+    out = np.empty((rows, stride), np.uint8)
+    _load().or_pack_rows(_p(codes), rows, row_len, bits, _p(out), stride)
+    return out
+
+
+def unpack_rows(packed, row_len: int, bits: int) -> np.ndarray:
+    packed = _c(packed, np.uint8)
+    rows, stride = packed.shape
+    out = np.empty((rows, row_len), np.uint32)
+    _load().or_unpack_rows(_p(packed), rows, row_len, bits, stride, _p(out))
+    return out
+
+
+# -------------------------------------------------------------- kinematics
+def fk(robot, q, with_xform: bool = False):
+    """-> pos [n, S, 3] (and xform [n, J, 12]) in float64."""
+    q = _c(q, np.float32)
+    n = q.shape[0]
+    nj, ns = robot.joint_fixed.shape[0], robot.sphere_local.shape[0]
+    pos = np.empty((n, ns, 3), np.float64)
+    xf = np.empty((n, nj, 12), np.float64) if with_xform else None
+    _load().or_fk(nj, _p(_c(robot.joint_fixed, np.float32)), ns,
+                  _p(_c(robot.sphere_local, np.float32)),
+                  _p(_c(robot.sphere_link, np.int32)), _p(q), n, _p(xf), _p(pos))
+    return (pos, xf) if with_xform else pos
+
+
+def box_sdf(pose, half, pts):
+    """Per-row signed distance of point i to cuboid i -> (d [m], grad [m, 3])."""
+    pose = _c(pose, np.float32).reshape(-1, 12)
+    half = _c(half, np.float32).reshape(-1, 3)
+    pts = _c(pts, np.float64).reshape(-1, 3)
+    m = pts.shape[0]
+    d = np.empty(m, np.float64)
+    g = np.empty((m, 3), np.float64)
+    _load().or_box_sdf_batch(_p(pose), _p(half), _p(pts), m, _p(d), _p(g))
+    return d, g
+
+
+def scene_sdf(scene, pts):
+    pts = _c(pts, np.float64).reshape(-1, 3)
+    out = np.empty(pts.shape[0], np.float64)
+    _load().or_scene_sdf(scene.pose.shape[0], _p(_c(scene.pose, np.float32)),
+                         _p(_c(scene.half_ext, np.float32)), _p(pts),
+                         pts.shape[0], _p(out))
+    return out
+
+
+def collision(robot, scene, params, pos, kink_eps: float = 1e-4):
+    """-> dict(cost [n], dist [n, S], grad [n, S, 3], kink [n, S])."""
+    pos = _c(pos, np.float64)
+    n, ns = pos.shape[0], pos.shape[1]
+    cost = np.empty(n, np.float64)
+    dist = np.empty((n, ns), np.float64)
+    grad = np.empty((n, ns, 3), np.float64)
+    kink = np.empty((n, ns), np.int32)
+    pairs = _c(robot.pairs, np.int32).reshape(-1, 2)
+    _load().or_collision(ns, _p(_c(robot.sphere_local, np.float32)),
+                         pairs.shape[0], _p(pairs), scene.pose.shape[0],
+                         _p(_c(scene.pose, np.float32)),
+                         _p(_c(scene.half_ext, np.float32)),
+                         params.eta, params.eta_self, params.w_coll,
+                         params.w_self, _p(pos), n, _p(cost), _p(dist),
+                         _p(grad), _p(kink), kink_eps)
+    return {"cost": cost, "dist": dist, "grad": grad, "kink": kink.astype(bool)}
+
+
+def backward(robot, q, grad, dcost=None):
+    """-> jgrad [n, J] float64."""
+    q = _c(q, np.float32)
+    n = q.shape[0]
+    nj, ns = robot.joint_fixed.shape[0], robot.sphere_local.shape[0]
+    grad = _c(grad, np.float64)
+    dc = None if dcost is None else _c(dcost, np.float64)
+    out = np.empty((n, nj), np.float64)
+    _load().or_backward(nj, _p(_c(robot.joint_fixed, np.float32)), ns,
+                        _p(_c(robot.sphere_local, np.float32)),
+                        _p(_c(robot.sphere_link, np.int32)), _p(q), _p(grad),
+                        _p(dc), n, _p(out))
+    return out
+
+
+def cost_and_grad(robot, scene, params, q, dcost=None):
+    """The whole path in FP64: q -> (pos, collision dict, jgrad)."""
+    pos = fk(robot, q)
+    col = collision(robot, scene, params, pos)
+    jg = backward(robot, q, col["grad"], dcost)
+    return pos, col, jg

@@ -1,0 +1,430 @@
+/*
+ * FP64 CPU oracle for the VaPr batched cost-and-gradient path.
+ * TEST INFRASTRUCTURE ONLY (see vapr_oracle.h): plain loops in double
+ * precision, one configuration at a time, no blocking or fusion.
+ */
+#include "vapr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ========================================================================= */
+/* ExMy emulator.  Sec. IV-A: a format has 1 sign bit, E exponent bits and M
+ * mantissa bits.  Reading: IEEE-style bias 2^(E-1)-1 with subnormals; the
+ * conversion rounds to nearest, ties to even (Sec. V-B names the "_rn"
+ * intrinsics), in the subnormal range too; signed zero is kept.  E8M23 is
+ * float32 itself and passes through unchanged. */
+
+static int is_identity(int E, int M) { return E == 8 && M == 23; }
+
+typedef struct {
+  int E, M, bias, emin;      /* emin: exponent of the smallest normal */
+  uint32_t all_e, all_m;     /* all-ones exponent / mantissa fields */
+  uint32_t max_code;         /* largest finite magnitude */
+  uint32_t inf_code;         /* Inf magnitude (IEEE only) */
+  uint32_t nan_code;         /* code produced for a NaN input */
+  double max_val;
+  int overflow_to_inf;       /* IEEE without SAT */
+} or_fmt;
+
+static or_fmt fmt_info(int E, int M, unsigned flags) {
+  or_fmt f;
+  f.E = E;
+  f.M = M;
+  f.bias = (1 << (E - 1)) - 1;
+  f.emin = 1 - f.bias;
+  f.all_e = (1u << E) - 1u;
+  f.all_m = (1u << M) - 1u;
+  uint32_t emax_field, mmax;
+  if (flags & OR_IEEE) {
+    emax_field = f.all_e - 1u;
+    mmax = f.all_m;
+  } else if (flags & OR_FN) {
+    emax_field = f.all_e;
+    mmax = f.all_m - 1u;
+  } else {
+    emax_field = f.all_e;
+    mmax = f.all_m;
+  }
+  f.max_code = (emax_field << M) | mmax;
+  f.max_val = ldexp(1.0 + (double)mmax / ldexp(1.0, M), (int)emax_field - f.bias);
+  f.inf_code = f.all_e << M;
+  /* NaN input: the canonical positive NaN (all-ones exponent and mantissa)
+   * where the format has NaN; otherwise the largest positive finite value. */
+  f.nan_code = (flags & (OR_IEEE | OR_FN)) ? ((f.all_e << M) | f.all_m) : f.max_code;
+  f.overflow_to_inf = (flags & OR_IEEE) && !(flags & OR_SAT);
+  return f;
+}
+
+double or_exmy_max_finite(int E, int M, unsigned flags) {
+  if (is_identity(E, M)) return 3.4028234663852886e38;
+  return fmt_info(E, M, flags).max_val;
+}
+
+uint32_t or_exmy_encode(float xf, int E, int M, unsigned flags) {
+  if (is_identity(E, M)) {
+    uint32_t u;
+    memcpy(&u, &xf, 4);
+    return u;
+  }
+  or_fmt f = fmt_info(E, M, flags);
+  double x = (double)xf;
+  if (isnan(x)) return f.nan_code;
+  uint32_t s = signbit(x) ? (1u << (E + M)) : 0u;
+  double a = fabs(x);
+  if (isinf(a)) return s | (f.overflow_to_inf ? f.inf_code : f.max_code);
+  if (a == 0.0) return s;
+
+  /* Round a to the format's grid.  Within binade [2^e, 2^(e+1)) the spacing
+   * is 2^(e-M); below the smallest normal it stays 2^(emin-M).  The exponent
+   * is left unbounded above so that overflow is decided on the rounded
+   * value, as IEEE round-to-nearest does. */
+  int e2;
+  frexp(a, &e2); /* a = f * 2^e2, f in [0.5, 1) */
+  int e = e2 - 1;
+  int quantum_exp = (e < f.emin ? f.emin : e) - M;
+  double n = nearbyint(ldexp(a, -quantum_exp)); /* exact scaling; RNE */
+  double v = ldexp(n, quantum_exp);
+  if (v > f.max_val) return s | (f.overflow_to_inf ? f.inf_code : f.max_code);
+  if (v == 0.0) return s;
+
+  if (v < ldexp(1.0, f.emin)) /* subnormal: exponent field 0 */
+    return s | (uint32_t)ldexp(v, M - f.emin);
+  frexp(v, &e2);
+  e = e2 - 1;
+  uint32_t mant = (uint32_t)(ldexp(v, M - e) - ldexp(1.0, M));
+  return s | ((uint32_t)(e + f.bias) << M) | mant;
+}
+
+double or_exmy_decode(uint32_t code, int E, int M, unsigned flags) {
+  if (is_identity(E, M)) {
+    float x;
+    memcpy(&x, &code, 4);
+    return (double)x;
+  }
+  or_fmt f = fmt_info(E, M, flags);
+  double sign = ((code >> (E + M)) & 1u) ? -1.0 : 1.0;
+  uint32_t ef = (code >> M) & f.all_e;
+  uint32_t mf = code & f.all_m;
+  if ((flags & OR_IEEE) && ef == f.all_e) return mf ? NAN : sign * INFINITY;
+  if ((flags & OR_FN) && ef == f.all_e && mf == f.all_m) return NAN;
+  if (ef == 0) return sign * ldexp((double)mf, f.emin - M);
+  return sign * ldexp(1.0 + (double)mf / ldexp(1.0, M), (int)ef - f.bias);
+}
+
+void or_exmy_encode_batch(const float* x, int64_t n, int E, int M,
+                          unsigned flags, uint32_t* codes) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) codes[i] = or_exmy_encode(x[i], E, M, flags);
+}
+
+void or_exmy_encode_bits_range(uint32_t start, int64_t count, int E, int M,
+                               unsigned flags, uint32_t* codes) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < count; ++i) {
+    uint32_t u = start + (uint32_t)i;
+    float x;
+    memcpy(&x, &u, 4);
+    codes[i] = or_exmy_encode(x, E, M, flags);
+  }
+}
+
+void or_exmy_decode_batch(const uint32_t* codes, int64_t n, int E, int M,
+                          unsigned flags, double* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) out[i] = or_exmy_decode(codes[i], E, M, flags);
+}
+
+/* Sec. IV-A: one 32-bit register holds floor(32/bits) values. */
+void or_pack_rows(const uint32_t* codes, int64_t rows, int64_t row_len,
+                  int bits, uint8_t* dst, int64_t row_stride_bytes) {
+  int k = 32 / bits;
+  uint32_t mask = bits == 32 ? 0xffffffffu : ((1u << bits) - 1u);
+  for (int64_t r = 0; r < rows; ++r) {
+    uint8_t* row = dst + r * row_stride_bytes;
+    memset(row, 0, (size_t)row_stride_bytes);
+    for (int64_t i = 0; i < row_len; ++i) {
+      int64_t w = i / k;
+      int sh = bits * (int)(i % k);
+      uint32_t word;
+      memcpy(&word, row + 4 * w, 4);
+      word |= (codes[r * row_len + i] & mask) << sh;
+      memcpy(row + 4 * w, &word, 4);
+    }
+  }
+}
+
+void or_unpack_rows(const uint8_t* src, int64_t rows, int64_t row_len,
+                    int bits, int64_t row_stride_bytes, uint32_t* codes) {
+  int k = 32 / bits;
+  uint32_t mask = bits == 32 ? 0xffffffffu : ((1u << bits) - 1u);
+  for (int64_t r = 0; r < rows; ++r) {
+    const uint8_t* row = src + r * row_stride_bytes;
+    for (int64_t i = 0; i < row_len; ++i) {
+      uint32_t word;
+      memcpy(&word, row + 4 * (i / k), 4);
+      codes[r * row_len + i] = (word >> (bits * (int)(i % k))) & mask;
+    }
+  }
+}
+
+/* ========================================================================= */
+/* Kinematics with 4x4 homogeneous matrices, row-major. */
+
+static void mat4_identity(double A[16]) {
+  memset(A, 0, 16 * sizeof(double));
+  A[0] = A[5] = A[10] = A[15] = 1.0;
+}
+
+static void mat4_mul(const double A[16], const double B[16], double C[16]) {
+  double T[16];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 4; ++k) acc += A[4 * i + k] * B[4 * k + j];
+      T[4 * i + j] = acc;
+    }
+  memcpy(C, T, sizeof(T));
+}
+
+/* 3x4 table row (R row-major, then t) -> 4x4 */
+static void mat4_from_3x4(const float* m, double A[16]) {
+  mat4_identity(A);
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) A[4 * i + j] = (double)m[3 * i + j];
+    A[4 * i + 3] = (double)m[9 + i];
+  }
+}
+
+static void mat4_rot_z(double q, double A[16]) {
+  mat4_identity(A);
+  A[0] = cos(q);
+  A[1] = -sin(q);
+  A[4] = sin(q);
+  A[5] = cos(q);
+}
+
+/* all link transforms T_1..T_nj of one configuration, 4x4 each */
+static void chain(int nj, const float* joint_fixed, const float* q, double* T) {
+  double prev[16], F[16], Rz[16], A[16];
+  mat4_identity(prev);
+  for (int i = 0; i < nj; ++i) {
+    mat4_from_3x4(joint_fixed + 12 * i, F);
+    mat4_rot_z((double)q[i], Rz);
+    mat4_mul(F, Rz, A);
+    mat4_mul(prev, A, T + 16 * i);
+    memcpy(prev, T + 16 * i, sizeof(prev));
+  }
+}
+
+static void apply(const double A[16], const double p[3], double out[3]) {
+  for (int i = 0; i < 3; ++i)
+    out[i] = A[4 * i] * p[0] + A[4 * i + 1] * p[1] + A[4 * i + 2] * p[2] + A[4 * i + 3];
+}
+
+void or_fk(int nj, const float* joint_fixed, int ns, const float* sphere_local,
+           const int32_t* sphere_link, const float* q, int64_t n,
+           double* xform, double* pos) {
+#pragma omp parallel
+  {
+    double* T = (double*)malloc(sizeof(double) * 16 * (size_t)nj);
+#pragma omp for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+      chain(nj, joint_fixed, q + (int64_t)nj * c, T);
+      if (xform) {
+        for (int i = 0; i < nj; ++i) {
+          double* out = xform + ((int64_t)nj * c + i) * 12;
+          for (int r = 0; r < 3; ++r) {
+            for (int k = 0; k < 3; ++k) out[3 * r + k] = T[16 * i + 4 * r + k];
+            out[9 + r] = T[16 * i + 4 * r + 3];
+          }
+        }
+      }
+      for (int s = 0; s < ns; ++s) {
+        double p[3] = {sphere_local[4 * s], sphere_local[4 * s + 1], sphere_local[4 * s + 2]};
+        apply(T + 16 * (sphere_link[s] - 1), p, pos + ((int64_t)ns * c + s) * 3);
+      }
+    }
+    free(T);
+  }
+}
+
+/* ========================================================================= */
+/* Oriented-box signed distance.  x = R^T (c - t), u = |x| - h,
+ * d = |max(u, 0)| + min(max_k u_k, 0).  Gradient (world frame): outside,
+ * R (sgn(x) * max(u, 0)) / |max(u, 0)|; inside or on the surface,
+ * R sgn(x_k) e_k with k = argmax_k u_k (lowest k on ties, sgn(0) = +1).
+ * *branch_margin receives the distance to the nearest gradient
+ * discontinuity: the top-two gap of u and |x_k| inside, +inf outside. */
+static double box_sdf(const float* pose, const float* half, const double c[3],
+                      double grad[3], double* branch_margin) {
+  double R[9], t[3], h[3], x[3], u[3], gl[3];
+  for (int i = 0; i < 9; ++i) R[i] = pose[i];
+  for (int i = 0; i < 3; ++i) {
+    t[i] = pose[9 + i];
+    h[i] = half[i];
+  }
+  for (int k = 0; k < 3; ++k) {
+    x[k] = 0.0;
+    for (int i = 0; i < 3; ++i) x[k] += R[3 * i + k] * (c[i] - t[i]);
+    u[k] = fabs(x[k]) - h[k];
+  }
+  double d;
+  int outside = u[0] > 0.0 || u[1] > 0.0 || u[2] > 0.0;
+  if (outside) {
+    double v[3], nrm = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      v[k] = u[k] > 0.0 ? u[k] : 0.0;
+      nrm += v[k] * v[k];
+    }
+    nrm = sqrt(nrm);
+    d = nrm;
+    for (int k = 0; k < 3; ++k) gl[k] = (x[k] >= 0.0 ? 1.0 : -1.0) * v[k] / nrm;
+    *branch_margin = INFINITY;
+  } else {
+    int ks = 0;
+    for (int k = 1; k < 3; ++k)
+      if (u[k] > u[ks]) ks = k;
+    d = u[ks];
+    double gap = INFINITY;
+    for (int k = 0; k < 3; ++k)
+      if (k != ks && u[ks] - u[k] < gap) gap = u[ks] - u[k];
+    *branch_margin = fmin(gap, fabs(x[ks]));
+    for (int k = 0; k < 3; ++k) gl[k] = 0.0;
+    gl[ks] = x[ks] >= 0.0 ? 1.0 : -1.0;
+  }
+  for (int i = 0; i < 3; ++i) grad[i] = R[3 * i] * gl[0] + R[3 * i + 1] * gl[1] + R[3 * i + 2] * gl[2];
+  return d;
+}
+
+void or_box_sdf_batch(const float* pose, const float* half, const double* pts,
+                      int64_t m, double* d, double* grad) {
+  for (int64_t i = 0; i < m; ++i) {
+    double margin;
+    d[i] = box_sdf(pose + 12 * i, half + 3 * i, pts + 3 * i, grad + 3 * i, &margin);
+  }
+}
+
+void or_scene_sdf(int no, const float* pose, const float* half,
+                  const double* pts, int64_t m, double* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < m; ++i) {
+    double best = INFINITY, g[3], margin;
+    for (int o = 0; o < no; ++o) {
+      double d = box_sdf(pose + 12 * o, half + 3 * o, pts + 3 * i, g, &margin);
+      if (d < best) best = d;
+    }
+    out[i] = best;
+  }
+}
+
+/* ========================================================================= */
+/* Collision cost and its gradient with respect to the sphere centres.
+ * Reading: the environment term sums the hinge over all cuboids (the paper
+ * does not say sum, min or max); the hinge's subgradient at exactly zero
+ * penetration is 0; a self pair at zero distance contributes no gradient. */
+void or_collision(int ns, const float* sphere_local, int npairs,
+                  const int32_t* pairs, int no, const float* pose,
+                  const float* half, double eta, double eta_s, double w_c,
+                  double w_s, const double* pos, int64_t n, double* cost,
+                  double* dist, double* grad, int32_t* kink, double kink_eps) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t c = 0; c < n; ++c) {
+    const double* P = pos + (int64_t)ns * 3 * c;
+    double* G = grad + (int64_t)ns * 3 * c;
+    int32_t* K = kink ? kink + (int64_t)ns * c : NULL;
+    double total = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      double r = sphere_local[4 * s + 3];
+      double Ds = 0.0, gs[3] = {0.0, 0.0, 0.0};
+      int flag = 0;
+      for (int o = 0; o < no; ++o) {
+        double gd[3], margin;
+        double d = box_sdf(pose + 12 * o, half + 3 * o, P + 3 * s, gd, &margin);
+        double pen = r + eta - d;
+        if (fabs(pen) < kink_eps) flag = 1;
+        if (pen > 0.0) {
+          Ds += pen;
+          for (int k = 0; k < 3; ++k) gs[k] -= gd[k];
+          if (margin < kink_eps) flag = 1;
+        }
+      }
+      dist[(int64_t)ns * c + s] = Ds;
+      for (int k = 0; k < 3; ++k) G[3 * s + k] = w_c * gs[k];
+      total += w_c * Ds;
+      if (K) K[s] = flag;
+    }
+    for (int p = 0; p < npairs; ++p) {
+      int i = pairs[2 * p], j = pairs[2 * p + 1];
+      double diff[3], d2 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        diff[k] = P[3 * i + k] - P[3 * j + k];
+        d2 += diff[k] * diff[k];
+      }
+      double dd = sqrt(d2);
+      double pen = sphere_local[4 * i + 3] + sphere_local[4 * j + 3] + eta_s - dd;
+      if (K && (fabs(pen) < kink_eps || (pen > 0.0 && dd < kink_eps))) K[i] = K[j] = 1;
+      if (pen > 0.0) {
+        total += w_s * pen;
+        if (dd > 0.0) {
+          for (int k = 0; k < 3; ++k) {
+            G[3 * i + k] -= w_s * diff[k] / dd;
+            G[3 * j + k] += w_s * diff[k] / dd;
+          }
+        }
+      }
+    }
+    cost[c] = total;
+  }
+}
+
+/* ========================================================================= */
+/* Backward kinematics: dc_s/dq_j = a_j x (c_s - o_j) for every sphere on a
+ * link at or beyond joint j (a revolute joint turns everything after it),
+ * so dC/dq_j = sum_s G_s . (a_j x (c_s - o_j)). */
+void or_backward(int nj, const float* joint_fixed, int ns,
+                 const float* sphere_local, const int32_t* sphere_link,
+                 const float* q, const double* grad, const double* dcost,
+                 int64_t n, double* jgrad) {
+#pragma omp parallel
+  {
+    double* T = (double*)malloc(sizeof(double) * 16 * (size_t)nj);
+#pragma omp for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+      chain(nj, joint_fixed, q + (int64_t)nj * c, T);
+      double scale = dcost ? dcost[c] : 1.0;
+      for (int j = 0; j < nj; ++j) {
+        const double* Tj = T + 16 * j;
+        double a[3] = {Tj[2], Tj[6], Tj[10]};  /* z column */
+        double o[3] = {Tj[3], Tj[7], Tj[11]};  /* origin */
+        double acc = 0.0;
+        for (int s = 0; s < ns; ++s) {
+          if (sphere_link[s] - 1 < j) continue;
+          double p[3] = {sphere_local[4 * s], sphere_local[4 * s + 1], sphere_local[4 * s + 2]};
+          double cs[3], rel[3], dc[3];
+          apply(T + 16 * (sphere_link[s] - 1), p, cs);
+          for (int k = 0; k < 3; ++k) rel[k] = cs[k] - o[k];
+          dc[0] = a[1] * rel[2] - a[2] * rel[1];
+          dc[1] = a[2] * rel[0] - a[0] * rel[2];
+          dc[2] = a[0] * rel[1] - a[1] * rel[0];
+          const double* g = grad + ((int64_t)ns * c + s) * 3;
+          acc += g[0] * dc[0] + g[1] * dc[1] + g[2] * dc[2];
+        }
+        jgrad[(int64_t)nj * c + j] = scale * acc;
+      }
+    }
+    free(T);
+  }
+}

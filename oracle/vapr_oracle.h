@@ -1,0 +1,110 @@
+/*
+ * FP64 CPU oracle for the VaPr batched cost-and-gradient path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; the two meet only through
+ * the seeded inputs of paper_2310_07854_gb300/synth.py.
+ *
+ * What it computes (paper: Sec. III-B iteration steps 2, 3 and 5; Sec. III-C
+ * large tensors; Sec. IV-A data formats; Sec. V-B conversion):
+ *   - forward kinematics of a serial revolute chain to sphere centres,
+ *   - the oriented-box signed distance and its gradient,
+ *   - the environment-collision and self-collision costs and their gradient
+ *     with respect to the sphere centres,
+ *   - the joint-space gradient (backward kinematics),
+ *   - an emulator of every ExMy storage format (round to nearest even).
+ * The paper prints none of these formulas (it relies on CuRobo); each
+ * function states the reading it follows.  Everything is computed in double
+ * precision from float32 inputs.
+ *
+ * Parity status: every function below is pinned by tests/test_oracle_*.py
+ * (closed forms, finite differences, rigid-motion invariance, brute force,
+ * library casts, exhaustive code-point checks).
+ */
+#ifndef VAPR_ORACLE_H
+#define VAPR_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Special-value classes of an ExMy format (Sec. IV-A gives only bit counts;
+ * these are the readings, chosen to agree with IEEE half/bfloat16 and the
+ * OCP 8/6/4-bit formats):
+ *   OR_IEEE: the all-ones exponent encodes Inf (mantissa 0) and NaN.
+ *   OR_FN:   no Inf; all-ones exponent with all-ones mantissa is NaN.
+ *   neither: every code is a finite number.
+ *   OR_SAT:  overflow and Inf clamp to the largest finite magnitude
+ *            (formats without Inf always clamp). */
+#define OR_IEEE 1u
+#define OR_FN 2u
+#define OR_SAT 4u
+
+/* ---- ExMy emulator (Sec. IV-A, Sec. V-B "_rn") ---------------------------- */
+uint32_t or_exmy_encode(float x, int E, int M, unsigned flags);
+double or_exmy_decode(uint32_t code, int E, int M, unsigned flags);
+double or_exmy_max_finite(int E, int M, unsigned flags);
+void or_exmy_encode_batch(const float* x, int64_t n, int E, int M,
+                          unsigned flags, uint32_t* codes);
+/* encodes the float32 values whose bit patterns are start, start+1, ... */
+void or_exmy_encode_bits_range(uint32_t start, int64_t count, int E, int M,
+                               unsigned flags, uint32_t* codes);
+void or_exmy_decode_batch(const uint32_t* codes, int64_t n, int E, int M,
+                          unsigned flags, double* out);
+/* k = floor(32/bits) codes per little-endian 32-bit word, value i of a row
+ * in word i/k at bit bits*(i%k); unused bits and padding words are zero. */
+void or_pack_rows(const uint32_t* codes, int64_t rows, int64_t row_len,
+                  int bits, uint8_t* dst, int64_t row_stride_bytes);
+void or_unpack_rows(const uint8_t* src, int64_t rows, int64_t row_len,
+                    int bits, int64_t row_stride_bytes, uint32_t* codes);
+
+/* ---- kinematics (Sec. II-B, Sec. III-B step 2) ----------------------------- */
+/* T_0 = I, T_i = T_{i-1} F_i Rz(q_i); c_s = T_link(s) [p_s; 1].
+ * joint_fixed [nj][12]: row-major 3x3 then translation.  sphere_local [ns][4]
+ * (x, y, z, r); sphere_link [ns] in 1..nj.  xform [n][nj][12] (may be NULL),
+ * pos [n][ns][3]. */
+void or_fk(int nj, const float* joint_fixed, int ns, const float* sphere_local,
+           const int32_t* sphere_link, const float* q, int64_t n,
+           double* xform, double* pos);
+
+/* ---- oriented-box signed distance ---------------------------------------- */
+/* pose [m][12] (row-major R, then centre t), half [m][3], pts [m][3]
+ * -> d [m], grad [m][3] (world-frame gradient of d). */
+void or_box_sdf_batch(const float* pose, const float* half, const double* pts,
+                      int64_t m, double* d, double* grad);
+
+/* ---- collision cost (Sec. III-B step 3, Sec. III-C) ----------------------- */
+/* D_s = sum_o max(0, r_s + eta - d_o(c_s));
+ * P_ij = max(0, r_i + r_j + eta_s - |c_i - c_j|) over the listed pairs;
+ * C = w_c sum_s D_s + w_s sum_ij P_ij;  G_s = dC/dc_s.
+ * kink [n][ns] (may be NULL) is set to 1 for spheres within kink_eps of a
+ * point where G is discontinuous (hinge activation, inside-argmax tie). */
+void or_collision(int ns, const float* sphere_local, int npairs,
+                  const int32_t* pairs, int no, const float* pose,
+                  const float* half, double eta, double eta_s, double w_c,
+                  double w_s, const double* pos, int64_t n, double* cost,
+                  double* dist, double* grad, int32_t* kink, double kink_eps);
+
+/* ---- backward kinematics (Sec. III-B step 5) ------------------------------ */
+/* J_j = dC * sum_{s: link(s) >= j} G_s . (a_j x (c_s - o_j)), with a_j the
+ * z-axis and o_j the origin of T_j, both from FK recomputed in FP64.
+ * dcost may be NULL (then 1). */
+void or_backward(int nj, const float* joint_fixed, int ns,
+                 const float* sphere_local, const int32_t* sphere_link,
+                 const float* q, const double* grad, const double* dcost,
+                 int64_t n, double* jgrad);
+
+/* ---- scene signed distance (surrogate labels) ----------------------------- */
+/* sdf(p) = min_o d_o(p) */
+void or_scene_sdf(int no, const float* pose, const float* half,
+                  const double* pts, int64_t m, double* out);
+
+int or_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
