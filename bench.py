@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput of the VaPr cost-and-gradient step on GB300.
+
+One step = FK -> collision cost (environment + self) -> backward to joint
+gradients over one batch of joint configurations, i.e. iteration steps 2,
+3-4 and 5 of Sec. III-B, through the C ABI of libvapr.so.
+
+Default workload: 1024 trajectories x 32 timesteps = 32768 configurations
+of the seeded 7-joint, 52-sphere arm against 40 oriented cuboids (1.7 M
+sphere evaluations per step).  Inputs are synthetic (the paper's Franka
+model and MotionBenchMaker scenes are not available) and resident in HBM;
+an L2-sized buffer is rewritten before every timed step, outside the timed
+events.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2310_07854_gb300 import formats as F  # noqa: E402
+from paper_2310_07854_gb300 import synth  # noqa: E402
+
+WORKLOAD = "particle_32768"
+VAPR_TABLE = "P=E5M10,D=E2M1,G=E2M1,J=E4M3"
+METRIC = "configs/s for FK+collision cost+grad"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="vapr", choices=["vapr", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(synth.WORKLOADS))
+    ap.add_argument("--table", default=VAPR_TABLE, help="format table of the VaPr leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dram-scale", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--configs", type=int, default=0,
+                    help="override the batch size (configurations per GPU)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------ cpu baseline
+def cpu_baseline(workload_name: str, seconds: float) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: whole batches of the
+    same workload until at least ``seconds`` of CPU time have passed."""
+    import oracle
+    w = synth.make_workload(workload_name)
+    oracle.build()
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.cost_and_grad(w.robot, w.scene, w.params, w.q)
+        done += w.n
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": "configs/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{done // w.n} full batches of {w.n} configurations of {workload_name} "
+                      f"(FP64 FK + collision + backward, OpenMP over configurations), "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.workload, max(args.cpu_seconds, 5.0))
+    steps_time = args.steps * (synth.make_workload(args.workload).n / cb["value"])
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "configs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * steps_time / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "global_batch": synth.make_workload(args.workload).n,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "configs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ timing
+def time_steps(ev, q, n, steps, warmup, flush_buf, torch):
+    """Device times (ms) of each step and of each kernel in it.
+
+    The step is one CUDA-graph replay (FK, collision, backward: no host work
+    between the kernels); CUDA events on the launching stream bracket it,
+    and external events captured inside the graph mark the kernel
+    boundaries.  The L2 flush runs before each step, outside the events."""
+    st = torch.cuda.current_stream()
+    g, inner = ev.capture(q, n, timing_events=True)
+    per = {"fk": [], "collision": [], "backward": [], "step": []}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for i in range(warmup + steps):
+        flush_buf.add_(1)
+        e0.record(st)
+        g.replay()
+        e1.record(st)
+        st.synchronize()
+        if i < warmup:
+            continue
+        per["step"].append(e0.elapsed_time(e1))
+        if inner:
+            per["fk"].append(inner[0].elapsed_time(inner[1]))
+            per["collision"].append(inner[1].elapsed_time(inner[2]))
+            per["backward"].append(inner[2].elapsed_time(inner[3]))
+    if not inner:  # per-kernel times from single-kernel graphs
+        for name, fn in (("fk", lambda: ev.fk(q, n)), ("collision", lambda: ev.collision(n)),
+                         ("backward", lambda: ev.backward(q, n))):
+            gk = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gk):
+                fn()
+            for i in range(warmup + steps):
+                flush_buf.add_(1)
+                e0.record(st)
+                gk.replay()
+                e1.record(st)
+                st.synchronize()
+                if i >= warmup:
+                    per[name].append(e0.elapsed_time(e1))
+    return per
+
+
+def kernel_traffic(stage: str, table: str):
+    """DRAM bytes per configuration from a committed ncu summary, if one
+    exists for the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2310_07854_gb300", "csrc", {"fk": "fk.cu", "collision": "collision.cu",
+                                                                  "backward": "backward.cu"}[stage])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = data.get(f"{stage}:{table}")
+    if not ent or ent.get("source_sha") != h:
+        return None
+    return ent.get("dram_bytes_per_config")
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    world, rank, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU fallback)")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+        pg = dist
+    from paper_2310_07854_gb300 import binding as B
+    from paper_2310_07854_gb300.path import Evaluator
+    B.lib()
+
+    w = synth.make_workload(args.workload)
+    if args.configs:
+        w.q = synth.make_q(500, args.configs)
+        w.n_traj = max(1, args.configs // w.horizon)
+    if rank:  # weak scaling: every rank evaluates its own batch of the same size
+        w.q = synth.make_q(1000 + rank, w.n)
+    n = w.n
+    q = torch.as_tensor(w.q, device="cuda")
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.zeros(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    vtable = F.FormatTable.parse(args.table)
+    ev32 = Evaluator(w.robot, w.scene, w.params, n, F.FP32_TABLE)
+    evv = Evaluator(ev32.robot, ev32.scene, w.params, n, vtable)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+
+    def max_over_ranks(x):
+        if not pg:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    peaks, peak_kind = measured_peaks()
+    barrier()
+    with ClockSampler(local) as clk:
+        per32 = time_steps(ev32, q, n, args.steps, args.warmup, flush, torch)
+        perv = time_steps(evv, q, n, args.steps, args.warmup, flush, torch)
+    barrier()
+    clocks = clk.summary()
+    t32 = max_over_ranks(sum(per32["step"]))
+    tv = max_over_ranks(sum(perv["step"]))
+    value = world * n * args.steps / (t32 / 1000.0)
+    value_v = world * n * args.steps / (tv / 1000.0)
+
+    # error of the VaPr table against the FP32 path (decoded by the CUDA unpacker)
+    def decoded(ev):
+        S, J = ev.robot.n_spheres, ev.robot.n_joints
+        out = {}
+        for name, buf, L, f in (("pos", ev.pos, 3 * S, ev.table.pos), ("dist", ev.dist, S, ev.table.dist),
+                                ("grad", ev.grad, 3 * S, ev.table.grad), ("jgrad", ev.jgrad, J, ev.table.jgrad)):
+            o = torch.empty((n, L), dtype=torch.float32, device="cuda")
+            B.vapr_unpack(buf, n, L, f, o)
+            out[name] = o
+        out["cost"] = ev.cost[:n].clone()
+        return out
+    a, b = decoded(ev32), decoded(evv)
+    err = {k: float((a[k] - b[k]).abs().max()) for k in a}
+    err_scale = {k: float(a[k].abs().max()) for k in a}
+
+    # roofline of the dominant kernel (FP32 table)
+    bpc = ev32.bytes_per_config()
+    avg = {k: statistics.mean(v) for k, v in per32.items() if k != "step"}
+    dom = max(avg, key=avg.get)
+    ach = bpc[dom] * n / (avg[dom] / 1000.0) / 1e9
+    traffic = kernel_traffic(dom, "fp32")
+    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_source": peak_kind,
+            "traffic": None if traffic is None else traffic * n,
+            "algorithmic_bytes_per_launch": bpc[dom] * n}
+    stages = {}
+    for ev_, per_, name in ((ev32, per32, "fp32"), (evv, perv, "vapr")):
+        bp = ev_.bytes_per_config()
+        stages[name] = {k: {"ms": statistics.mean(per_[k]),
+                            "GB/s": bp[k] * n / (statistics.mean(per_[k]) / 1000.0) / 1e9,
+                            "hbm_frac": bp[k] * n / (statistics.mean(per_[k]) / 1000.0) / 1e9 / peaks["hbm_gbs"],
+                            "bytes_per_config": bp[k]} for k in ("fk", "collision", "backward")}
+
+    # end to end: pinned host q -> device -> path -> cost and J back to the host
+    qh = torch.as_tensor(w.q).pin_memory()
+    ch = torch.empty(n, dtype=torch.float32).pin_memory()
+    jh = torch.empty((n, w.robot.n_joints), dtype=torch.float32).pin_memory()
+    qd = torch.empty_like(q)
+    for _ in range(args.warmup):
+        ev32.step_host(qh, ch, jh, qd)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ev32.step_host(qh, ch, jh, qd)
+    barrier()
+    te = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * n * args.steps / te, "unit": "configs/s",
+           "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(ch.numel() * 4 + jh.numel() * 4),
+           "launches_per_step": 4}
+
+    dram = None
+    if not args.no_dram_scale:
+        nb = 1 << 20
+        qb = torch.as_tensor(synth.make_q(77, nb), device="cuda")
+        ebig = Evaluator(ev32.robot, ev32.scene, w.params, nb, F.FP32_TABLE)
+        pb = time_steps(ebig, qb, nb, 3, 2, flush, torch)
+        ebv = Evaluator(ev32.robot, ev32.scene, w.params, nb, vtable)
+        pbv = time_steps(ebv, qb, nb, 3, 2, flush, torch)
+        dram = {"n_configs": nb}
+        for ev_, per_, name in ((ebig, pb, "fp32"), (ebv, pbv, "vapr")):
+            bp = ev_.bytes_per_config()
+            dram[name] = {"configs_per_s": nb * 3 / (sum(per_["step"]) / 1000.0)}
+            for k in ("fk", "collision", "backward"):
+                ms = statistics.mean(per_[k])
+                dram[name][k] = {"ms": ms, "hbm_frac": bp[k] * nb / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]}
+        del ebig, ebv, qb
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(args.workload, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "configs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t32 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "global_batch": world * n, "trajectories": w.n_traj,
+                       "horizon": w.horizon, "spheres": w.robot.n_spheres,
+                       "cuboids": w.scene.n_cuboids, "self_pairs": w.robot.n_pairs,
+                       "table": str(F.FP32_TABLE), "parallelism": f"replicas{world}",
+                       "l2": "flushed before every step (2 x L2 buffer rewritten outside the timed events)"},
+            "roofline": roof,
+            "vapr": {"table": str(vtable), "value": value_v, "unit": "configs/s",
+                     "speedup_vs_fp32": value_v / value, "ms_per_step": tv / args.steps,
+                     "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale},
+            "stages": stages,
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cb,
+            "dram_scale": dram,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * vapr.h -- C ABI of the GB300 (sm_103a) VaPr cost-and-gradient library.
+ *
+ * The path (arXiv 2310.07854, Sec. III-B iteration steps 2, 3 and 5, and
+ * Sec. III-C's large tensors):
+ *   vapr_fk              joint configurations q -> sphere centres P (and
+ *                        optionally link transforms T)        [out_spheres]
+ *   vapr_collision_cost  P -> per-configuration cost C, per-sphere
+ *                        penetration D and dC/dP = G          [closest_pt,
+ *                        out_vec, grad_out_spheres]
+ *   vapr_backward        G (and q or T) -> joint gradient J
+ *   vapr_pack / unpack   float32 <-> ExMy storage (Sec. IV-A, Sec. V-B)
+ * P, D, G, J and T are stored in per-tensor ExMy formats (a
+ * vapr_format_table), packed floor(32/bits) values per 32-bit word.
+ *
+ * Conventions shared by every entry point:
+ *  - Memory: every array argument is a DEVICE pointer unless its comment
+ *    says host.  The caller owns all buffers and the stream; the library
+ *    allocates nothing on these calls.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Calls only enqueue work and return; they do not synchronise.
+ *  - Errors: arguments are checked before anything is enqueued and a bad
+ *    one returns a status without launching.  A launch failure returns
+ *    VAPR_ERR_CUDA (vapr_last_cuda_error() gives the cudaError_t).  Nothing
+ *    aborts, throws or traps.  Table contents on the device (link indices,
+ *    pair indices) cannot be checked without a copy: kernels clamp them into
+ *    range so no access leaves its buffer; vapr_robot_check() validates
+ *    them once, synchronously, at set-up.
+ *  - n == 0 is a no-op returning VAPR_OK.
+ *  - Packed layout: row r of a packed tensor starts at byte
+ *    r * vapr_packed_row_bytes(row_len, fmt).  Value i of a row sits in
+ *    32-bit little-endian word i / k, bits [b*(i%k), b*(i%k)+b) with
+ *    b = 1+E+M and k = floor(32/b); unused high bits and the row's padding
+ *    words are written as zero.  The row stride is a multiple of 16 bytes,
+ *    and packed buffers must be 16-byte aligned.  FP32/FP16/BF16 rows are
+ *    therefore plain float/half/bfloat16 arrays.
+ *  - Rounding: float32 -> ExMy rounds to nearest, ties to even, with
+ *    subnormals (Sec. V-B names the "_rn" conversions).  Special values
+ *    follow the format's flags (VAPR_FMT_*); vapr_format_default() gives
+ *    the flags of every standard format.
+ */
+#ifndef VAPR_H
+#define VAPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VAPR_OK = 0,
+  VAPR_ERR_INVALID_ARG = 1,        /* NULL, negative or out-of-range argument */
+  VAPR_ERR_UNSUPPORTED_FORMAT = 2, /* (E, M, flags) not a storage format */
+  VAPR_ERR_MISALIGNED = 3,         /* pointer alignment rule broken */
+  VAPR_ERR_CUDA = 4,               /* a CUDA call failed */
+  VAPR_ERR_TIMEOUT = 5,            /* a device-side wait hit its limit */
+  VAPR_ERR_TOO_LARGE = 6           /* a size above a documented maximum */
+} vapr_status;
+
+/* Limits of one robot / scene. */
+#define VAPR_MAX_JOINTS 16
+#define VAPR_MAX_SPHERES 128
+#define VAPR_MAX_PAIRS 8128   /* all pairs of 128 spheres */
+#define VAPR_MAX_CUBOIDS 1024
+
+/* Format flags (Sec. IV-A gives only bit counts; these classes are the
+ * reading that agrees with IEEE half/bfloat16 and the OCP 8/6/4-bit types):
+ *   VAPR_FMT_IEEE      all-ones exponent = Inf (mantissa 0) / NaN;
+ *   VAPR_FMT_FN        no Inf, all-ones exponent and mantissa = NaN;
+ *   neither            every code is finite;
+ *   VAPR_FMT_SATFINITE overflow and Inf clamp to the largest finite value
+ *                      (formats without Inf always clamp).
+ * A NaN input becomes the format's positive all-ones NaN code, or its
+ * largest positive finite value when it has no NaN. */
+#define VAPR_FMT_IEEE 1u
+#define VAPR_FMT_FN 2u
+#define VAPR_FMT_SATFINITE 4u
+
+typedef struct {
+  uint8_t exp_bits;  /* E: 2..8 */
+  uint8_t man_bits;  /* M: 1..23; 1+E+M <= 16, or E8M23 (float32) */
+  uint8_t flags;     /* VAPR_FMT_* ; 8-exponent-bit formats need IEEE */
+  uint8_t reserved;  /* 0 */
+} vapr_format;
+
+/* Storage format of each large tensor (Sec. III-C, Table II). */
+typedef struct {
+  vapr_format pos;    /* P: sphere centres [n][S*3]         (out_spheres) */
+  vapr_format dist;   /* D: per-sphere penetration [n][S]                */
+  vapr_format grad;   /* G: dC/dP [n][S*3]  (grad_out_spheres/closest_pt) */
+  vapr_format jgrad;  /* J: joint gradient [n][J]                        */
+  vapr_format xform;  /* T: link transforms [n][J*12], R row-major then t */
+} vapr_format_table;
+
+/* A serial revolute arm (Sec. II-B robot kinematics).  T_0 = I and
+ * T_i = T_{i-1} * F_i * Rz(q_i); sphere s rides on link sphere_link[s],
+ * c_s = T_link * [p_s; 1].  All arrays are device memory, 16-byte aligned. */
+typedef struct {
+  int32_t n_joints;            /* J, 1..VAPR_MAX_JOINTS */
+  int32_t n_spheres;           /* S, 1..VAPR_MAX_SPHERES */
+  int32_t n_pairs;             /* self-collision pairs, 0..VAPR_MAX_PAIRS */
+  int32_t reserved;            /* 0 */
+  const float* joint_fixed;    /* [J][12]: F_i, row-major 3x3 then translation */
+  const float* sphere_local;   /* [S][4]: x, y, z in the link frame, radius */
+  const int32_t* sphere_link;  /* [S]: link index 1..J */
+  const int32_t* pairs;        /* [n_pairs][2]: sphere indices */
+} vapr_robot;
+
+/* Oriented cuboids (device memory, 16-byte aligned). */
+typedef struct {
+  int32_t n_cuboids;           /* O, 0..VAPR_MAX_CUBOIDS */
+  int32_t reserved;
+  const float* pose;           /* [O][12]: rotation row-major, then centre */
+  const float* half_ext;       /* [O][3]: half side lengths (> 0) */
+} vapr_scene;
+
+/* Cost parameters (reading; the paper delegates them to CuRobo):
+ * D_s = sum_o max(0, r_s + eta - d_o(c_s)),
+ * P_ij = max(0, r_i + r_j + eta_self - |c_i - c_j|),
+ * C = w_coll * sum_s D_s + w_self * sum_pairs P_ij. */
+typedef struct {
+  float eta, eta_self, w_coll, w_self;
+} vapr_cost_params;
+
+/* ---- status and formats (host only, no device work) ---------------------- */
+const char* vapr_status_string(vapr_status s);
+/* the cudaError_t of the last VAPR_ERR_CUDA on this thread (0 if none) */
+int vapr_last_cuda_error(void);
+/* flags of the standard format with these bit counts (see VAPR_FMT_*) */
+vapr_format vapr_format_default(int exp_bits, int man_bits);
+/* 1 if f is a supported storage format, else 0 */
+int vapr_format_supported(vapr_format f);
+/* bytes of one packed row of row_len values (a multiple of 16; 0 when
+ * row_len <= 0 or f is unsupported) */
+size_t vapr_packed_row_bytes(int64_t row_len, vapr_format f);
+
+/* Copies the robot's device tables to the host and checks them: links in
+ * 1..J, pair indices in 0..S-1 and distinct, radii >= 0.  Synchronous.
+ * Returns VAPR_ERR_INVALID_ARG on the first bad entry. */
+vapr_status vapr_robot_check(const vapr_robot* robot);
+
+/* ---- converters (Sec. IV-A packing, Sec. V-B "_rn" conversion) ---------- */
+/* src: float32 [rows][row_len] (contiguous, 4-byte aligned);
+ * dst: packed rows (16-byte aligned), row stride vapr_packed_row_bytes. */
+vapr_status vapr_pack(const float* src, int64_t rows, int64_t row_len,
+                      vapr_format f, void* dst, void* stream);
+/* the inverse: exact decode of every code to float32 */
+vapr_status vapr_unpack(const void* src, int64_t rows, int64_t row_len,
+                        vapr_format f, float* dst, void* stream);
+
+/* ---- the path ------------------------------------------------------------ */
+/* Forward kinematics (Sec. II-B; iteration step 2 of Sec. III-B).
+ * q: float32 [n][J] (4-byte aligned).  pos_packed: [n] rows of S*3 values
+ * in table->pos.  xform_packed: NULL, or [n] rows of J*12 values (T_1..T_J,
+ * each R row-major then t) in table->xform. */
+vapr_status vapr_fk(const vapr_robot* robot, const float* q, int64_t n,
+                    const vapr_format_table* table, void* pos_packed,
+                    void* xform_packed, void* stream);
+
+/* Collision cost (iteration steps 3-4 of Sec. III-B).
+ * pos_packed: [n] rows of S*3 values in table->pos.
+ * cost: NULL or float32 [n].  dist_packed: NULL or [n] rows of S values in
+ * table->dist.  grad_packed: NULL or [n] rows of S*3 values of dC/dc_s in
+ * table->grad.  The environment sum runs over every cuboid; the hinge's
+ * gradient at exactly zero penetration is 0, and a self pair at zero
+ * distance adds no gradient. */
+vapr_status vapr_collision_cost(const vapr_robot* robot, const vapr_scene* scene,
+                                const vapr_cost_params* params,
+                                const void* pos_packed, int64_t n,
+                                const vapr_format_table* table, float* cost,
+                                void* dist_packed, void* grad_packed,
+                                void* stream);
+
+/* Backward kinematics (iteration step 5 of Sec. III-B):
+ * J_j = dC * sum_{s: link(s) >= j} G_s . (a_j x (c_s - o_j)), a_j and o_j
+ * the z-axis and origin of T_j.  q: float32 [n][J].  xform_packed: NULL to
+ * recompute FK from q, else the rows vapr_fk wrote (table->xform).
+ * grad_packed: rows of S*3 values in table->grad.  dcost: NULL (= 1) or
+ * float32 [n].  jgrad_packed: [n] rows of J values in table->jgrad.
+ * Zero gradient words are skipped (Sec. III-C sparsity). */
+vapr_status vapr_backward(const vapr_robot* robot, const float* q,
+                          const void* xform_packed, const void* grad_packed,
+                          const float* dcost, int64_t n,
+                          const vapr_format_table* table, void* jgrad_packed,
+                          void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VAPR_H */

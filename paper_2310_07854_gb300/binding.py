@@ -1,0 +1,256 @@
+"""Thin Python binding of libvapr.so (include/vapr.h).
+
+Each ``vapr_*`` function here has the name and argument order of the C entry
+point it calls; it only marshals arguments (torch tensors -> device
+pointers, the current CUDA stream) and turns a non-OK status into
+``VaprError``.  All computation happens in the CUDA library: there is no
+CPU or PyTorch fallback, and loading fails loudly when the library is
+missing.
+
+``DeviceRobot`` / ``DeviceScene`` hold the device copies of the seeded
+tables (``synth``) together with the C structs that point at them, and
+``alloc_packed`` sizes packed buffers with ``vapr_packed_row_bytes``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import formats as F
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvapr.so")
+
+OK = 0
+STATUS_NAMES = {0: "VAPR_OK", 1: "VAPR_ERR_INVALID_ARG", 2: "VAPR_ERR_UNSUPPORTED_FORMAT",
+                3: "VAPR_ERR_MISALIGNED", 4: "VAPR_ERR_CUDA", 5: "VAPR_ERR_TIMEOUT",
+                6: "VAPR_ERR_TOO_LARGE"}
+MAX_JOINTS, MAX_SPHERES, MAX_PAIRS, MAX_CUBOIDS = 16, 128, 8128, 1024
+
+
+class VaprError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _load().vapr_status_string(status).decode()
+        extra = ""
+        if status == 4:
+            extra = f" (cudaError {_load().vapr_last_cuda_error()})"
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}{extra}")
+
+
+# ------------------------------------------------------------------ structs
+class vapr_format(ctypes.Structure):
+    _fields_ = [("exp_bits", ctypes.c_uint8), ("man_bits", ctypes.c_uint8),
+                ("flags", ctypes.c_uint8), ("reserved", ctypes.c_uint8)]
+
+
+class vapr_format_table(ctypes.Structure):
+    _fields_ = [(n, vapr_format) for n in ("pos", "dist", "grad", "jgrad", "xform")]
+
+
+class vapr_robot(ctypes.Structure):
+    _fields_ = [("n_joints", ctypes.c_int32), ("n_spheres", ctypes.c_int32),
+                ("n_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("joint_fixed", ctypes.c_void_p), ("sphere_local", ctypes.c_void_p),
+                ("sphere_link", ctypes.c_void_p), ("pairs", ctypes.c_void_p)]
+
+
+class vapr_scene(ctypes.Structure):
+    _fields_ = [("n_cuboids", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pose", ctypes.c_void_p), ("half_ext", ctypes.c_void_p)]
+
+
+class vapr_cost_params(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_float), ("eta_self", ctypes.c_float),
+                ("w_coll", ctypes.c_float), ("w_self", ctypes.c_float)]
+
+
+# Every exported symbol, with (restype, argtypes).
+_P = ctypes.c_void_p
+_i64 = ctypes.c_int64
+SIGNATURES = {
+    "vapr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "vapr_last_cuda_error": (ctypes.c_int, []),
+    "vapr_format_default": (vapr_format, [ctypes.c_int, ctypes.c_int]),
+    "vapr_format_supported": (ctypes.c_int, [vapr_format]),
+    "vapr_packed_row_bytes": (ctypes.c_size_t, [_i64, vapr_format]),
+    "vapr_robot_check": (ctypes.c_int, [ctypes.POINTER(vapr_robot)]),
+    "vapr_pack": (ctypes.c_int, [_P, _i64, _i64, vapr_format, _P, _P]),
+    "vapr_unpack": (ctypes.c_int, [_P, _i64, _i64, vapr_format, _P, _P]),
+    "vapr_fk": (ctypes.c_int, [ctypes.POINTER(vapr_robot), _P, _i64,
+                               ctypes.POINTER(vapr_format_table), _P, _P, _P]),
+    "vapr_collision_cost": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
+                                           ctypes.POINTER(vapr_cost_params), _P, _i64,
+                                           ctypes.POINTER(vapr_format_table), _P, _P, _P, _P]),
+    "vapr_backward": (ctypes.c_int, [ctypes.POINTER(vapr_robot), _P, _P, _P, _P, _i64,
+                                     ctypes.POINTER(vapr_format_table), _P, _P]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _load():
+    """Loads libvapr.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libvapr.so is missing at {LIB_PATH}; run build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def lib():
+    return _load()
+
+
+# ----------------------------------------------------------------- helpers
+def to_c_format(f: F.Fmt) -> vapr_format:
+    return vapr_format(f.E, f.M, f.flags, 0)
+
+
+def to_c_table(t) -> vapr_format_table:
+    if isinstance(t, vapr_format_table):
+        return t
+    return vapr_format_table(*(to_c_format(getattr(t, n)) for n in F.TENSORS))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise VaprError(status, where)
+
+
+class DeviceRobot:
+    """Device copies of a ``synth.Robot`` and the ``vapr_robot`` pointing at them."""
+
+    def __init__(self, robot, device="cuda"):
+        import torch
+        self.host = robot
+        self.joint_fixed = torch.as_tensor(np.ascontiguousarray(robot.joint_fixed, np.float32), device=device)
+        self.sphere_local = torch.as_tensor(np.ascontiguousarray(robot.sphere_local, np.float32), device=device)
+        self.sphere_link = torch.as_tensor(np.ascontiguousarray(robot.sphere_link, np.int32), device=device)
+        pairs = np.ascontiguousarray(robot.pairs, np.int32).reshape(-1, 2)
+        self.pairs = torch.as_tensor(pairs if pairs.size else np.zeros((1, 2), np.int32), device=device)
+        self.c = vapr_robot(robot.n_joints, robot.n_spheres, int(pairs.shape[0]), 0,
+                            self.joint_fixed.data_ptr(), self.sphere_local.data_ptr(),
+                            self.sphere_link.data_ptr(), self.pairs.data_ptr())
+
+    @property
+    def n_joints(self):
+        return self.c.n_joints
+
+    @property
+    def n_spheres(self):
+        return self.c.n_spheres
+
+
+class DeviceScene:
+    def __init__(self, scene, device="cuda"):
+        import torch
+        self.host = scene
+        n = scene.n_cuboids
+        pose = np.ascontiguousarray(scene.pose, np.float32).reshape(-1, 12)
+        half = np.ascontiguousarray(scene.half_ext, np.float32).reshape(-1, 3)
+        if n == 0:  # keep valid (unused) pointers for an empty scene
+            pose, half = np.zeros((1, 12), np.float32), np.zeros((1, 3), np.float32)
+        self.pose = torch.as_tensor(pose, device=device)
+        self.half_ext = torch.as_tensor(half, device=device)
+        self.c = vapr_scene(n, 0, self.pose.data_ptr(), self.half_ext.data_ptr())
+
+
+def cost_params(p) -> vapr_cost_params:
+    return vapr_cost_params(p.eta, p.eta_self, p.w_coll, p.w_self)
+
+
+def packed_row_bytes(row_len: int, fmt: F.Fmt) -> int:
+    return int(_load().vapr_packed_row_bytes(row_len, to_c_format(fmt)))
+
+
+def alloc_packed(rows: int, row_len: int, fmt: F.Fmt, device="cuda"):
+    """A uint8 tensor [rows, row_bytes] for packed rows (16-byte aligned)."""
+    import torch
+    rb = packed_row_bytes(row_len, fmt)
+    return torch.empty((rows, rb), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------- entry points (same names)
+def vapr_format_default(exp_bits: int, man_bits: int) -> vapr_format:
+    return _load().vapr_format_default(exp_bits, man_bits)
+
+
+def vapr_format_supported(f: vapr_format) -> bool:
+    return bool(_load().vapr_format_supported(f))
+
+
+def vapr_packed_row_bytes(row_len: int, f: vapr_format) -> int:
+    return int(_load().vapr_packed_row_bytes(row_len, f))
+
+
+def vapr_robot_check(robot: DeviceRobot):
+    _check(_load().vapr_robot_check(ctypes.byref(robot.c)), "vapr_robot_check")
+
+
+def vapr_pack(src, rows, row_len, fmt: F.Fmt, dst, stream=None):
+    _check(_load().vapr_pack(_ptr(src), rows, row_len, to_c_format(fmt), _ptr(dst),
+                             _stream(stream)), "vapr_pack")
+
+
+def vapr_unpack(src, rows, row_len, fmt: F.Fmt, dst, stream=None):
+    _check(_load().vapr_unpack(_ptr(src), rows, row_len, to_c_format(fmt), _ptr(dst),
+                               _stream(stream)), "vapr_unpack")
+
+
+def vapr_fk(robot: DeviceRobot, q, n, table: F.FormatTable, pos_packed, xform_packed=None,
+            stream=None):
+    ct = to_c_table(table)
+    _check(_load().vapr_fk(ctypes.byref(robot.c), _ptr(q), n, ctypes.byref(ct),
+                           _ptr(pos_packed), _ptr(xform_packed), _stream(stream)), "vapr_fk")
+
+
+def vapr_collision_cost(robot: DeviceRobot, scene: DeviceScene, params, pos_packed, n,
+                        table: F.FormatTable, cost=None, dist_packed=None, grad_packed=None,
+                        stream=None):
+    ct = to_c_table(table)
+    cp = params if isinstance(params, vapr_cost_params) else cost_params(params)
+    _check(_load().vapr_collision_cost(ctypes.byref(robot.c), ctypes.byref(scene.c),
+                                       ctypes.byref(cp), _ptr(pos_packed), n, ctypes.byref(ct),
+                                       _ptr(cost), _ptr(dist_packed), _ptr(grad_packed),
+                                       _stream(stream)), "vapr_collision_cost")
+
+
+def vapr_backward(robot: DeviceRobot, q, xform_packed, grad_packed, dcost, n,
+                  table: F.FormatTable, jgrad_packed, stream=None):
+    ct = to_c_table(table)
+    _check(_load().vapr_backward(ctypes.byref(robot.c), _ptr(q), _ptr(xform_packed),
+                                 _ptr(grad_packed), _ptr(dcost), n, ctypes.byref(ct),
+                                 _ptr(jgrad_packed), _stream(stream)), "vapr_backward")

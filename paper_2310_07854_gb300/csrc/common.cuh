@@ -1,0 +1,62 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/vapr.h"
+#include "exmy.cuh"
+
+namespace vapr {
+
+// Robot tables as the kernels read them (device pointers).
+struct RobotArgs {
+  int J, S, NP;
+  const float* joint_fixed;   // [J][12]
+  const float* sphere_local;  // [S][4]
+  const int32_t* sphere_link; // [S]
+  const int32_t* pairs;       // [NP][2]
+};
+
+struct SceneArgs {
+  int O;
+  const float* pose;  // [O][12]
+  const float* half;  // [O][3]
+};
+
+// A packed tensor: base pointer, row stride in bytes, format.
+struct Packed {
+  uint8_t* ptr;
+  int64_t stride;
+  DevFmt f;
+};
+
+DevFmt make_dev_fmt(vapr_format f);
+int sm_count();  // SMs of the current device (cached per device)
+// Resident blocks per SM of `fn` at `threads` and `smem` dynamic bytes on the
+// current device.  The first call for a (kernel, device, smem) also raises
+// the kernel's dynamic shared-memory limit; later calls hit a cache, so a
+// launch costs no attribute or occupancy query.  Returns <= 0 on error.
+int blocks_per_sm(const void* fn, int threads, size_t smem);
+
+cudaError_t launch_fk(const RobotArgs& r, const float* q, int64_t n, Packed pos,
+                      Packed xform, cudaStream_t st);
+cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc,
+                             const vapr_cost_params& p, Packed pos, int64_t n,
+                             float* cost, Packed dist, Packed grad, cudaStream_t st);
+cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform,
+                            Packed grad, const float* dcost, int64_t n,
+                            Packed jgrad, cudaStream_t st);
+cudaError_t launch_pack(const float* src, int64_t rows, int64_t row_len, Packed dst,
+                        cudaStream_t st);
+cudaError_t launch_unpack(Packed src, int64_t rows, int64_t row_len, float* dst,
+                          cudaStream_t st);
+
+// Clamps a device-table index into [lo, hi] so that a bad table can give a
+// wrong answer but never an out-of-bounds access.
+__device__ __forceinline__ int clampi(int v, int lo, int hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+}  // namespace vapr

@@ -1,0 +1,123 @@
+"""The whole cost-and-gradient step through the C ABI.
+
+``Evaluator`` owns the packed intermediate tensors of one batch size and
+runs FK -> collision cost -> backward (iteration steps 2, 3-4 and 5 of
+Sec. III-B) with a per-tensor format table.  ``step_host`` is the end-to-end
+call: joint configurations in pinned host memory go to the device, the path
+runs, and costs and joint gradients come back to the host.
+"""
+from __future__ import annotations
+
+from . import binding as B
+from . import formats as F
+
+
+class Evaluator:
+    def __init__(self, robot, scene, params, n_max: int, table: F.FormatTable = F.FP32_TABLE,
+                 recompute_fk: bool = True, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.robot = robot if isinstance(robot, B.DeviceRobot) else B.DeviceRobot(robot, device)
+        self.scene = scene if isinstance(scene, B.DeviceScene) else B.DeviceScene(scene, device)
+        self.params = B.cost_params(params)
+        self.table = table
+        self.ctable = B.to_c_table(table)  # built once: calls pass the C struct
+        self.recompute_fk = recompute_fk
+        self.n_max = n_max
+        S, J = self.robot.n_spheres, self.robot.n_joints
+        self.pos = B.alloc_packed(n_max, 3 * S, table.pos, device)
+        self.dist = B.alloc_packed(n_max, S, table.dist, device)
+        self.grad = B.alloc_packed(n_max, 3 * S, table.grad, device)
+        self.jgrad = B.alloc_packed(n_max, J, table.jgrad, device)
+        self.xform = None if recompute_fk else B.alloc_packed(n_max, 12 * J, table.xform, device)
+        self.cost = torch.empty(n_max, dtype=torch.float32, device=device)
+        self.jgrad_f32 = torch.empty((n_max, J), dtype=torch.float32, device=device)
+
+    # ---- device-resident stages
+    def forward(self, q, n: int, stream=None):
+        self.fk(q, n, stream)
+        self.collision(n, stream)
+        return self.cost[:n]
+
+    def fk(self, q, n: int, stream=None):
+        B.vapr_fk(self.robot, q, n, self.ctable, self.pos, self.xform, stream)
+
+    def collision(self, n: int, stream=None):
+        B.vapr_collision_cost(self.robot, self.scene, self.params, self.pos, n, self.ctable,
+                              self.cost, self.dist, self.grad, stream)
+
+    def backward(self, q, n: int, dcost=None, stream=None):
+        B.vapr_backward(self.robot, q, self.xform, self.grad, dcost, n, self.ctable,
+                        self.jgrad, stream)
+        return self.jgrad[:n]
+
+    def unpack_jgrad(self, n: int, stream=None):
+        B.vapr_unpack(self.jgrad, n, self.robot.n_joints, self.table.jgrad, self.jgrad_f32, stream)
+        return self.jgrad_f32[:n]
+
+    def step(self, q, n: int, dcost=None, stream=None):
+        """FK, collision cost, backward: three kernel launches."""
+        self.forward(q, n, stream)
+        self.backward(q, n, dcost, stream)
+
+    def capture(self, q, n: int, dcost=None, timing_events: bool = False):
+        """Captures one step in a CUDA graph (replay = three kernel launches,
+        no host work in between).  With ``timing_events`` the graph also
+        records four external timing events at the kernel boundaries;
+        returns (graph, events or None)."""
+        torch = self.torch
+        self.step(q, n, dcost)  # first launches fill the library's launch caches
+        torch.cuda.synchronize()
+        evs = None
+        if timing_events:
+            try:
+                evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(4)]
+            except TypeError:  # a torch without external events
+                evs = None
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            if evs:
+                evs[0].record()
+            self.fk(q, n)
+            if evs:
+                evs[1].record()
+            self.collision(n)
+            if evs:
+                evs[2].record()
+            self.backward(q, n, dcost)
+            if evs:
+                evs[3].record()
+        return g, evs
+
+    # ---- end to end from host memory
+    def step_host(self, q_host, cost_host, jgrad_host, q_dev, stream=None):
+        """q_host (pinned float32 [n, J]) -> cost_host [n], jgrad_host [n, J]
+        float32 (pinned).  Copies and kernels are enqueued on one stream;
+        the call returns after the results are on the host."""
+        torch = self.torch
+        n = q_host.shape[0]
+        st = stream or torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            q_dev[:n].copy_(q_host, non_blocking=True)
+            self.step(q_dev, n, None, st)
+            self.unpack_jgrad(n, st)
+            cost_host.copy_(self.cost[:n], non_blocking=True)
+            jgrad_host.copy_(self.jgrad_f32[:n], non_blocking=True)
+        st.synchronize()
+        return cost_host, jgrad_host
+
+    def bytes_per_config(self) -> dict:
+        """Algorithmic bytes per configuration of each stage (packed rows,
+        unpadded; robot and scene tables excluded)."""
+        S, J = self.robot.n_spheres, self.robot.n_joints
+        t = self.table
+        P = t.pos.row_bytes_unpadded(3 * S)
+        D = t.dist.row_bytes_unpadded(S)
+        G = t.grad.row_bytes_unpadded(3 * S)
+        Jb = t.jgrad.row_bytes_unpadded(J)
+        T = t.xform.row_bytes_unpadded(12 * J)
+        q = 4 * J
+        fk = q + P + (0 if self.recompute_fk else T)
+        coll = P + D + G + 4
+        bw = q + G + 4 + Jb + (0 if self.recompute_fk else T)
+        return {"fk": fk, "collision": coll, "backward": bw, "total": fk + coll + bw}

@@ -1,0 +1,102 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/vapr.h declares, and rejects bad arguments before any device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2310_07854_gb300 import binding as B
+from paper_2310_07854_gb300 import formats as F
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "vapr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vapr_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = B.lib()
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in B.SIGNATURES, f"binding lacks {name}"
+
+
+def test_status_strings():
+    lib = B.lib()
+    for code in range(7):
+        assert lib.vapr_status_string(code)
+    assert b"unknown" in lib.vapr_status_string(99)
+
+
+def test_default_formats_match_host_logic():
+    for f in F.search_set() + [F.fmt(5, 9), F.fmt(6, 8), F.fmt(6, 6)]:
+        c = B.vapr_format_default(f.E, f.M)
+        assert (c.exp_bits, c.man_bits, c.flags) == (f.E, f.M, f.flags), f
+        assert B.vapr_format_supported(c)
+        for n in (0, 1, 7, 52, 156, 1000):
+            assert B.vapr_packed_row_bytes(n, c) == (f.row_bytes(n) if n else 0)
+
+
+def test_unsupported_formats():
+    bad = [(1, 2, 4), (9, 2, 4), (5, 20, 1), (8, 3, 4), (8, 23, 4), (4, 3, 3), (4, 3, 8)]
+    for E, M, fl in bad:
+        assert not B.vapr_format_supported(B.vapr_format(E, M, fl, 0)), (E, M, fl)
+    assert not B.vapr_format_supported(B.vapr_format(4, 3, 6, 1))  # reserved != 0
+    assert B.vapr_packed_row_bytes(10, B.vapr_format(9, 2, 4, 0)) == 0
+
+
+def _robot_struct(**kw):
+    base = dict(n_joints=7, n_spheres=52, n_pairs=10, reserved=0, joint_fixed=256,
+                sphere_local=512, sphere_link=768, pairs=1024)
+    base.update(kw)
+    return B.vapr_robot(**base)
+
+
+def test_argument_checks_before_launch():
+    lib = B.lib()
+    t = B.to_c_table(F.FP32_TABLE)
+    r = _robot_struct()
+    byref = ctypes.byref
+    INVALID, UNSUP, MIS, TOO = 1, 2, 3, 6
+    # null robot / table
+    assert lib.vapr_fk(None, 256, 4, byref(t), 256, None, None) == INVALID
+    assert lib.vapr_fk(byref(r), 256, 4, None, 256, None, None) == INVALID
+    # counts out of range
+    for kw in (dict(n_joints=0), dict(n_joints=17), dict(n_spheres=129), dict(n_pairs=-1),
+               dict(n_pairs=8129), dict(sphere_local=0)):
+        assert lib.vapr_fk(byref(_robot_struct(**kw)), 256, 4, byref(t), 256, None, None) == INVALID
+    # n == 0 is a no-op, n < 0 invalid
+    assert lib.vapr_fk(byref(r), 256, 0, byref(t), 256, None, None) == 0
+    assert lib.vapr_fk(byref(r), 256, -1, byref(t), 256, None, None) == INVALID
+    # misaligned packed buffer / table
+    assert lib.vapr_fk(byref(r), 256, 4, byref(t), 264, None, None) == MIS
+    assert lib.vapr_fk(byref(_robot_struct(sphere_local=520)), 256, 4, byref(t), 256, None, None) == MIS
+    # unsupported format in the table
+    bad = B.to_c_table(F.FP32_TABLE)
+    bad.grad = B.vapr_format(9, 1, 4, 0)
+    assert lib.vapr_fk(byref(r), 256, 4, byref(bad), 256, None, None) == UNSUP
+    # collision: too many cuboids, missing scene
+    p = B.vapr_cost_params(0.02, 0.01, 1.0, 1.0)
+    sc = B.vapr_scene(1025, 0, 256, 256)
+    assert lib.vapr_collision_cost(byref(r), byref(sc), byref(p), 256, 4, byref(t),
+                                   None, None, None, None) == TOO
+    assert lib.vapr_collision_cost(byref(r), None, byref(p), 256, 4, byref(t),
+                                   None, None, None, None) == INVALID
+    sc = B.vapr_scene(8, 0, 256, 256)
+    assert lib.vapr_collision_cost(byref(r), byref(sc), byref(p), 0, 4, byref(t),
+                                   None, None, None, None) == INVALID
+    # backward needs q or stored transforms, and aligned outputs
+    assert lib.vapr_backward(byref(r), None, None, 256, None, 4, byref(t), 256, None) == INVALID
+    assert lib.vapr_backward(byref(r), 256, None, 256, None, 4, byref(t), 260, None) == MIS
+    # converters
+    f = B.vapr_format(2, 1, 4, 0)
+    assert lib.vapr_pack(256, 4, 10, f, 8, None) == MIS
+    assert lib.vapr_pack(256, -1, 10, f, 256, None) == INVALID
+    assert lib.vapr_pack(256, 0, 10, f, 256, None) == 0
+    assert lib.vapr_unpack(256, 4, 10, B.vapr_format(9, 1, 4, 0), 256, None) == UNSUP
