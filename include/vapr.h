@@ -136,6 +136,11 @@ int vapr_format_supported(vapr_format f);
  * row_len <= 0 or f is unsupported) */
 size_t vapr_packed_row_bytes(int64_t row_len, vapr_format f);
 
+/* Reads and clears the sticky error word of kernels with device-side waits
+ * (the TMA staging wait of vapr_backward): *code receives VAPR_ERR_TIMEOUT
+ * if a wait hit its limit since the last call, else 0.  Synchronous. */
+vapr_status vapr_device_error(int32_t* code);
+
 /* Copies the robot's device tables to the host and checks them: links in
  * 1..J, pair indices in 0..S-1 and distinct, radii >= 0.  Synchronous.
  * Returns VAPR_ERR_INVALID_ARG on the first bad entry. */
@@ -185,6 +190,28 @@ vapr_status vapr_backward(const vapr_robot* robot, const float* q,
                           const float* dcost, int64_t n,
                           const vapr_format_table* table, void* jgrad_packed,
                           void* stream);
+
+/* ---- the whole step ------------------------------------------------------ */
+/* Device workspace that vapr_cost_grad needs for n configurations: the
+ * packed P and G rows, each region 256-byte aligned.  0 on a bad argument. */
+size_t vapr_cost_grad_workspace_bytes(const vapr_robot* robot, int64_t n,
+                                      const vapr_format_table* table);
+
+/* One step of the path, q -> (C, D, J): vapr_fk, vapr_collision_cost and
+ * vapr_backward back to back on `stream` (iteration steps 2-5 of
+ * Sec. III-B), with P and G held in the caller's workspace in their table
+ * formats and FK recomputed in backward.  q: float32 [n][J].  dcost: NULL
+ * (= 1) or float32 [n].  cost: float32 [n] (required).  dist_packed: NULL or
+ * [n] rows of S values (table->dist).  jgrad_packed: [n] rows of J values
+ * (table->jgrad).  workspace: device, 256-byte aligned, at least
+ * vapr_cost_grad_workspace_bytes(robot, n, table) bytes (INVALID_ARG if
+ * smaller); its contents are scratch.  Results equal the three calls made
+ * one by one. */
+vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
+                           const vapr_cost_params* params, const float* q, int64_t n,
+                           const vapr_format_table* table, const float* dcost, float* cost,
+                           void* dist_packed, void* jgrad_packed, void* workspace,
+                           size_t workspace_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -78,6 +78,7 @@ SIGNATURES = {
     "vapr_format_supported": (ctypes.c_int, [vapr_format]),
     "vapr_packed_row_bytes": (ctypes.c_size_t, [_i64, vapr_format]),
     "vapr_robot_check": (ctypes.c_int, [ctypes.POINTER(vapr_robot)]),
+    "vapr_device_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
     "vapr_pack": (ctypes.c_int, [_P, _i64, _i64, vapr_format, _P, _P]),
     "vapr_unpack": (ctypes.c_int, [_P, _i64, _i64, vapr_format, _P, _P]),
     "vapr_fk": (ctypes.c_int, [ctypes.POINTER(vapr_robot), _P, _i64,
@@ -87,6 +88,12 @@ SIGNATURES = {
                                            ctypes.POINTER(vapr_format_table), _P, _P, _P, _P]),
     "vapr_backward": (ctypes.c_int, [ctypes.POINTER(vapr_robot), _P, _P, _P, _P, _i64,
                                      ctypes.POINTER(vapr_format_table), _P, _P]),
+    "vapr_cost_grad_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(vapr_robot), _i64,
+                                                         ctypes.POINTER(vapr_format_table)]),
+    "vapr_cost_grad": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
+                                      ctypes.POINTER(vapr_cost_params), _P, _i64,
+                                      ctypes.POINTER(vapr_format_table), _P, _P, _P, _P, _P,
+                                      ctypes.c_size_t, _P]),
 }
 
 _lib = None
@@ -216,6 +223,13 @@ def vapr_packed_row_bytes(row_len: int, f: vapr_format) -> int:
     return int(_load().vapr_packed_row_bytes(row_len, f))
 
 
+def vapr_device_error() -> int:
+    """Reads and clears the sticky device error word (0 = none)."""
+    v = ctypes.c_int32(0)
+    _check(_load().vapr_device_error(ctypes.byref(v)), "vapr_device_error")
+    return int(v.value)
+
+
 def vapr_robot_check(robot: DeviceRobot):
     _check(_load().vapr_robot_check(ctypes.byref(robot.c)), "vapr_robot_check")
 
@@ -254,3 +268,27 @@ def vapr_backward(robot: DeviceRobot, q, xform_packed, grad_packed, dcost, n,
     _check(_load().vapr_backward(ctypes.byref(robot.c), _ptr(q), _ptr(xform_packed),
                                  _ptr(grad_packed), _ptr(dcost), n, ctypes.byref(ct),
                                  _ptr(jgrad_packed), _stream(stream)), "vapr_backward")
+
+
+def vapr_cost_grad_workspace_bytes(robot: DeviceRobot, n: int, table) -> int:
+    ct = to_c_table(table)
+    return int(_load().vapr_cost_grad_workspace_bytes(ctypes.byref(robot.c), n, ctypes.byref(ct)))
+
+
+def alloc_workspace(robot: DeviceRobot, n: int, table, device="cuda"):
+    """A device buffer of vapr_cost_grad_workspace_bytes (256-byte aligned:
+    torch's allocator aligns blocks to at least 512 bytes)."""
+    import torch
+    nbytes = max(vapr_cost_grad_workspace_bytes(robot, n, table), 256)
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def vapr_cost_grad(robot: DeviceRobot, scene: DeviceScene, params, q, n, table, dcost, cost,
+                   dist_packed, jgrad_packed, workspace, workspace_bytes=None, stream=None):
+    ct = to_c_table(table)
+    cp = params if isinstance(params, vapr_cost_params) else cost_params(params)
+    nbytes = workspace.numel() if workspace_bytes is None else workspace_bytes
+    _check(_load().vapr_cost_grad(ctypes.byref(robot.c), ctypes.byref(scene.c), ctypes.byref(cp),
+                                  _ptr(q), n, ctypes.byref(ct), _ptr(dcost), _ptr(cost),
+                                  _ptr(dist_packed), _ptr(jgrad_packed), _ptr(workspace),
+                                  nbytes, _stream(stream)), "vapr_cost_grad")

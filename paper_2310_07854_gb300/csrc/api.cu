@@ -110,13 +110,17 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
   if (!done) {  // allow up to the device's opt-in maximum once; launches use less
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess) {
+      cudaGetLastError();  // clear it: a later launch check must not see this
       return -1;
+    }
     raised.emplace_back(fn, dev);
   }
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess)
-    return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    blocks = 0;  // does not fit (e.g. too much shared memory): cache the answer
+  }
   cache.push_back(Entry{fn, dev, threads, smem, blocks});
   return blocks;
 }
@@ -142,33 +146,21 @@ __global__ void pack_kernel(const float* __restrict__ src, int64_t rows, int row
     const int64_t r = c / cpr;
     const int cc = (int)(c - r * cpr);
     const float* row = src + r * row_len;
-    auto get = [&](int i) { return row[i]; };
-    uint4 v;
-    v.x = pack_word(4 * cc + 0, row_len, dst.f, get);
-    v.y = pack_word(4 * cc + 1, row_len, dst.f, get);
-    v.z = pack_word(4 * cc + 2, row_len, dst.f, get);
-    v.w = pack_word(4 * cc + 3, row_len, dst.f, get);
-    *reinterpret_cast<uint4*>(dst.ptr + r * dst.stride + 16 * cc) = v;
+    *reinterpret_cast<uint4*>(dst.ptr + r * dst.stride + 16 * cc) =
+        pack_chunk_dyn(cc, row_len, dst.f, [&](int i) { return row[i]; });
   }
 }
 
 __global__ void unpack_kernel(Packed src, int64_t rows, int row_len, float* __restrict__ dst) {
   const int cpr = (int)(src.stride / 16);
   const int64_t total = rows * cpr;
-  const DevFmt& f = src.f;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = c / cpr;
     const int cc = (int)(c - r * cpr);
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(src.ptr + r * src.stride + 16 * cc));
-    const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
     float* row = dst + r * row_len;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i0 = (4 * cc + q) * f.k;
-      for (int j = 0; j < f.k; ++j)
-        if (i0 + j < row_len) row[i0 + j] = unpack_slot(w4[q], j, f);
-    }
+    unpack_chunk_dyn(v, cc, row_len, src.f, [&](int i, float x) { row[i] = x; });
   }
 }
 
@@ -272,6 +264,14 @@ int vapr_format_supported(vapr_format f) { return fmt_ok(f) ? 1 : 0; }
 
 size_t vapr_packed_row_bytes(int64_t row_len, vapr_format f) { return row_bytes(row_len, f); }
 
+vapr_status vapr_device_error(int32_t* code) {
+  if (!code) return VAPR_ERR_INVALID_ARG;
+  const int v = backward_device_error(true);
+  if (v < 0) return cuda_status(cudaErrorUnknown);
+  *code = v;
+  return VAPR_OK;
+}
+
 vapr_status vapr_robot_check(const vapr_robot* robot) {
   RobotArgs r;
   vapr_status st = check_robot(robot, &r);
@@ -364,6 +364,57 @@ vapr_status vapr_collision_cost(const vapr_robot* robot, const vapr_scene* scene
       r, sc, *params, packed(pos_packed, 3 * (int64_t)r.S, table->pos), n, cost,
       packed(dist_packed, r.S, table->dist), packed(grad_packed, 3 * (int64_t)r.S, table->grad),
       (cudaStream_t)stream));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t vapr_cost_grad_workspace_bytes(const vapr_robot* robot, int64_t n,
+                                      const vapr_format_table* table) {
+  RobotArgs r;
+  if (check_robot(robot, &r) != VAPR_OK || check_table(table) != VAPR_OK || n < 0) return 0;
+  const size_t P = row_bytes(3 * (int64_t)r.S, table->pos) * (size_t)n;
+  const size_t G = row_bytes(3 * (int64_t)r.S, table->grad) * (size_t)n;
+  return align256(P) + align256(G);
+}
+
+vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
+                           const vapr_cost_params* params, const float* q, int64_t n,
+                           const vapr_format_table* table, const float* dcost, float* cost,
+                           void* dist_packed, void* jgrad_packed, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+  RobotArgs r;
+  vapr_status st = check_robot(robot, &r);
+  if (st != VAPR_OK) return st;
+  if ((st = check_table(table)) != VAPR_OK) return st;
+  if (!scene || !params) return VAPR_ERR_INVALID_ARG;
+  if (scene->n_cuboids < 0) return VAPR_ERR_INVALID_ARG;
+  if (scene->n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
+  if (scene->n_cuboids > 0 && (!scene->pose || !scene->half_ext)) return VAPR_ERR_INVALID_ARG;
+  if (scene->n_cuboids > 0 && (!aligned(scene->pose, 16) || !aligned(scene->half_ext, 4)))
+    return VAPR_ERR_MISALIGNED;
+  if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n == 0) return VAPR_OK;
+  if (!q || !cost || !jgrad_packed || !workspace) return VAPR_ERR_INVALID_ARG;
+  if (workspace_bytes < vapr_cost_grad_workspace_bytes(robot, n, table)) return VAPR_ERR_INVALID_ARG;
+  if (!aligned(q, 4) || !aligned(cost, 4) || (dcost && !aligned(dcost, 4)) ||
+      !aligned(jgrad_packed, 16) || (dist_packed && !aligned(dist_packed, 16)) ||
+      !aligned(workspace, 256))
+    return VAPR_ERR_MISALIGNED;
+  SceneArgs sc;
+  sc.O = scene->n_cuboids;
+  sc.pose = scene->pose;
+  sc.half = scene->half_ext;
+  const cudaStream_t s = (cudaStream_t)stream;
+  uint8_t* ws = (uint8_t*)workspace;
+  Packed pos = packed(ws, 3 * (int64_t)r.S, table->pos);
+  Packed grad = packed(ws + align256((size_t)pos.stride * (size_t)n), 3 * (int64_t)r.S, table->grad);
+  Packed none = packed(nullptr, 12 * (int64_t)r.J, table->xform);
+  cudaError_t e = launch_fk(r, q, n, pos, none, s);
+  if (e == cudaSuccess)
+    e = launch_collision(r, sc, *params, pos, n, cost, packed(dist_packed, r.S, table->dist), grad, s);
+  if (e == cudaSuccess)
+    e = launch_backward(r, q, none, grad, dcost, n, packed(jgrad_packed, r.J, table->jgrad), s);
+  return cuda_status(e);
 }
 
 vapr_status vapr_backward(const vapr_robot* robot, const float* q, const void* xform_packed,

@@ -40,6 +40,8 @@ int sm_count();  // SMs of the current device (cached per device)
 // launch costs no attribute or occupancy query.  Returns <= 0 on error.
 int blocks_per_sm(const void* fn, int threads, size_t smem);
 
+int backward_device_error(bool reset);  // sticky device word of vapr_backward
+
 cudaError_t launch_fk(const RobotArgs& r, const float* q, int64_t n, Packed pos,
                       Packed xform, cudaStream_t st);
 cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc,

@@ -6,9 +6,8 @@
 //
 // A block takes tiles of FK_TILE configurations.  Each thread runs the joint
 // chain of one configuration and leaves its J transforms in shared memory;
-// then the whole block writes the tile's packed rows, which are contiguous
-// in global memory, with coalesced 16-byte stores (one 16-byte chunk of a
-// row per thread).
+// then the block writes the tile's packed rows: warps take rows, lanes take
+// the 32-bit words of a row, so every warp store is 128 contiguous bytes.
 #include "common.cuh"
 
 namespace vapr {
@@ -79,48 +78,43 @@ __global__ void __launch_bounds__(FK_TILE) fk_kernel(FkArgs a) {
     }
     __syncthreads();
 
-    // sphere centres: value i of a row is coordinate i % 3 of sphere i / 3
-    {
-      const int cpr = (int)(a.pos.stride / 16);
-      const int nv = 3 * S;
-      for (int c = threadIdx.x; c < rows * cpr; c += blockDim.x) {
-        const int r = c / cpr, cc = c - r * cpr;
-        const float4* T = sT + r * a.tstride;
-        auto get = [&](int i) {
-          const int s = i / 3, d = i - 3 * s;
-          const float4 row = T[3 * sLink[s] + d];
-          const float4 p = sSph[s];
-          return fmaf(row.x, p.x, fmaf(row.y, p.y, fmaf(row.z, p.z, row.w)));
-        };
-        uint4 v;
-        v.x = pack_word(4 * cc + 0, nv, a.pos.f, get);
-        v.y = pack_word(4 * cc + 1, nv, a.pos.f, get);
-        v.z = pack_word(4 * cc + 2, nv, a.pos.f, get);
-        v.w = pack_word(4 * cc + 3, nv, a.pos.f, get);
-        *reinterpret_cast<uint4*>(a.pos.ptr + (base + r) * a.pos.stride + 16 * cc) = v;
-      }
+    // Packed rows: warps take the tile's rows, lanes the words of a row, so
+    // each warp store covers 128 consecutive bytes.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    {  // sphere centres: value i of a row is coordinate i % 3 of sphere i / 3
+      const int words = (int)(a.pos.stride / 4), nv = 3 * S;
+      dispatch_kind(a.pos.f.kind, [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        for (int r = warp; r < rows; r += nwarps) {
+          const float4* T = sT + r * a.tstride;
+          uint32_t* out = reinterpret_cast<uint32_t*>(a.pos.ptr + (base + r) * a.pos.stride);
+          for (int w = lane; w < words; w += 32)
+            out[w] = pack_word_t<K>(w, nv, a.pos.f, [&](int i) {
+              const int s = i / 3, d = i - 3 * s;
+              const float4 row = T[3 * sLink[s] + d];
+              const float4 p = sSph[s];
+              return fmaf(row.x, p.x, fmaf(row.y, p.y, fmaf(row.z, p.z, row.w)));
+            });
+        }
+      });
     }
-    // link transforms: value i is element i % 12 (R row-major, then t) of T_{i/12}
-    if (a.xform.ptr) {
-      const int cpr = (int)(a.xform.stride / 16);
-      const int nv = 12 * J;
-      for (int c = threadIdx.x; c < rows * cpr; c += blockDim.x) {
-        const int r = c / cpr, cc = c - r * cpr;
-        const float4* T = sT + r * a.tstride;
-        auto get = [&](int i) {
-          const int j = i / 12, e = i - 12 * j;
-          const int d = e < 9 ? e / 3 : e - 9;
-          const int col = e < 9 ? e - 3 * d : 3;
-          const float4 row = T[3 * j + d];
-          return col == 0 ? row.x : col == 1 ? row.y : col == 2 ? row.z : row.w;
-        };
-        uint4 v;
-        v.x = pack_word(4 * cc + 0, nv, a.xform.f, get);
-        v.y = pack_word(4 * cc + 1, nv, a.xform.f, get);
-        v.z = pack_word(4 * cc + 2, nv, a.xform.f, get);
-        v.w = pack_word(4 * cc + 3, nv, a.xform.f, get);
-        *reinterpret_cast<uint4*>(a.xform.ptr + (base + r) * a.xform.stride + 16 * cc) = v;
-      }
+    if (a.xform.ptr) {  // link transforms: value i is element i % 12 (R row-major, t) of T_{i/12}
+      const int words = (int)(a.xform.stride / 4), nv = 12 * J;
+      dispatch_kind(a.xform.f.kind, [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        for (int r = warp; r < rows; r += nwarps) {
+          const float4* T = sT + r * a.tstride;
+          uint32_t* out = reinterpret_cast<uint32_t*>(a.xform.ptr + (base + r) * a.xform.stride);
+          for (int w = lane; w < words; w += 32)
+            out[w] = pack_word_t<K>(w, nv, a.xform.f, [&](int i) {
+              const int j = i / 12, e = i - 12 * j;
+              const int d = e < 9 ? e / 3 : e - 9;
+              const int col = e < 9 ? e - 3 * d : 3;
+              const float4 row = T[3 * j + d];
+              return col == 0 ? row.x : col == 1 ? row.y : col == 2 ? row.z : row.w;
+            });
+        }
+      });
     }
   }
 }

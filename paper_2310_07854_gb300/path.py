@@ -32,6 +32,7 @@ class Evaluator:
         self.xform = None if recompute_fk else B.alloc_packed(n_max, 12 * J, table.xform, device)
         self.cost = torch.empty(n_max, dtype=torch.float32, device=device)
         self.jgrad_f32 = torch.empty((n_max, J), dtype=torch.float32, device=device)
+        self.workspace = B.alloc_workspace(self.robot, n_max, table, device)
 
     # ---- device-resident stages
     def forward(self, q, n: int, stream=None):
@@ -89,6 +90,12 @@ class Evaluator:
                 evs[3].record()
         return g, evs
 
+    def cost_grad(self, q, n: int, dcost=None, stream=None):
+        """The whole step in one library call (vapr_cost_grad): cost [n] and
+        packed joint gradients, P and G in the evaluator's workspace."""
+        B.vapr_cost_grad(self.robot, self.scene, self.params, q, n, self.ctable, dcost,
+                         self.cost, self.dist, self.jgrad, self.workspace, stream=stream)
+
     # ---- end to end from host memory
     def step_host(self, q_host, cost_host, jgrad_host, q_dev, stream=None):
         """q_host (pinned float32 [n, J]) -> cost_host [n], jgrad_host [n, J]
@@ -99,7 +106,7 @@ class Evaluator:
         st = stream or torch.cuda.current_stream()
         with torch.cuda.stream(st):
             q_dev[:n].copy_(q_host, non_blocking=True)
-            self.step(q_dev, n, None, st)
+            self.cost_grad(q_dev, n, None, st)
             self.unpack_jgrad(n, st)
             cost_host.copy_(self.cost[:n], non_blocking=True)
             jgrad_host.copy_(self.jgrad_f32[:n], non_blocking=True)

@@ -100,3 +100,27 @@ def test_argument_checks_before_launch():
     assert lib.vapr_pack(256, -1, 10, f, 256, None) == INVALID
     assert lib.vapr_pack(256, 0, 10, f, 256, None) == 0
     assert lib.vapr_unpack(256, 4, 10, B.vapr_format(9, 1, 4, 0), 256, None) == UNSUP
+
+
+def test_cost_grad_workspace_and_checks():
+    lib = B.lib()
+    byref = ctypes.byref
+    r = _robot_struct()
+    for spec in ("", "P=E5M10,G=E2M1"):
+        t = F.FormatTable.parse(spec) if spec else F.FP32_TABLE
+        ct = B.to_c_table(t)
+        for n in (1, 7, 1000):
+            want = 0
+            for f in (t.pos, t.grad):
+                want += -(-f.row_bytes(156) * n // 256) * 256
+            assert lib.vapr_cost_grad_workspace_bytes(byref(r), n, byref(ct)) == want
+    ct = B.to_c_table(F.FP32_TABLE)
+    need = lib.vapr_cost_grad_workspace_bytes(byref(r), 10, byref(ct))
+    p = B.vapr_cost_params(0.02, 0.01, 1.0, 1.0)
+    sc = B.vapr_scene(8, 0, 256, 256)
+    args = lambda ws, nbytes, n=10: (byref(r), byref(sc), byref(p), 256, n, byref(ct), None, 256,
+                                     None, 256, ws, nbytes, None)
+    assert lib.vapr_cost_grad(*args(1024, need - 1)) == 1       # workspace too small
+    assert lib.vapr_cost_grad(*args(1040, need)) == 3           # not 256-byte aligned
+    assert lib.vapr_cost_grad(*args(None, need)) == 1
+    assert lib.vapr_cost_grad(*args(1024, 0, n=0)) == 0         # n == 0: no-op

@@ -1,0 +1,52 @@
+"""vapr_cost_grad (the whole step in one call, intermediates in a caller
+workspace) against the three entry points called one by one, and against
+the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_07854_gb300 import binding as B
+from paper_2310_07854_gb300 import formats as F
+from paper_2310_07854_gb300 import synth
+from parity import KINK_EPS, GpuPath, check_fp32, decode_packed, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("spec", ["", "P=E5M10,D=E2M1,G=E2M1,J=E4M3", "P=E6M6,G=E3M1,J=BF16"])
+@pytest.mark.parametrize("name", ["single_128", "particle_32768"])
+def test_cost_grad_equals_three_calls(name, spec):
+    import torch
+    w = synth.make_workload(name)
+    table = F.FormatTable.parse(spec) if spec else F.FP32_TABLE
+    gp = GpuPath(w.robot, w.scene, w.params)
+    q = to_dev(w.q)
+    dc = to_dev(synth.make_dcost(2, w.n))
+    pos, _ = gp.fk(q, w.n, table)
+    cost, dist, grad = gp.collision(pos, w.n, table)
+    jg = gp.backward(q, None, grad, dc, w.n, table)
+    ws = B.alloc_workspace(gp.rd, w.n, table)
+    ws.fill_(0x5A)  # scratch contents must not matter
+    cost2 = torch.empty_like(cost)
+    dist2 = torch.empty_like(dist)
+    jg2 = torch.empty_like(jg)
+    B.vapr_cost_grad(gp.rd, gp.sd, w.params, q, w.n, table, dc, cost2, dist2, jg2, ws)
+    assert torch.equal(cost, cost2) and torch.equal(dist, dist2) and torch.equal(jg, jg2)
+    assert B.vapr_device_error() == 0
+
+
+def test_cost_grad_fp32_parity():
+    import torch
+    w = synth.make_workload("sweep_1024")
+    rd, sd = B.DeviceRobot(w.robot), B.DeviceScene(w.scene)
+    q = to_dev(w.q)
+    cost = torch.empty(w.n, device="cuda")
+    jg = B.alloc_packed(w.n, 7, F.FP32)
+    ws = B.alloc_workspace(rd, w.n, F.FP32_TABLE)
+    B.vapr_cost_grad(rd, sd, w.params, q, w.n, F.FP32_TABLE, None, cost, None, jg, ws)
+    pos = oracle.fk(w.robot, w.q)
+    col = oracle.collision(w.robot, w.scene, w.params, pos, kink_eps=KINK_EPS)
+    want = oracle.backward(w.robot, w.q, col["grad"])
+    check_fp32(cost.cpu().numpy(), col["cost"], what="C")
+    ok = ~col["kink"].any(1)
+    check_fp32(decode_packed(jg, 7, F.FP32), want, mask=np.repeat(ok[:, None], 7, 1), what="J")

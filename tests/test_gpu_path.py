@@ -119,6 +119,7 @@ def test_whole_path_fp32(wl):
     assert cfg_ok.mean() > 0.5
     check_fp32(decode_packed(jg, J, F.FP32), wl["jg"], mask=np.repeat(cfg_ok[:, None], J, 1),
                what="J")
+    assert B.vapr_device_error() == 0  # no device-side wait timed out
 
 
 def test_whole_path_reduced_reports_error(wl):
