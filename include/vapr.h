@@ -213,6 +213,35 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
                            void* dist_packed, void* jgrad_packed, void* workspace,
                            size_t workspace_bytes, void* stream);
 
+/* ---- the whole step without allocation ------------------------------------ */
+/* Size of the library's fixed device scratch array (64 MiB per GPU that
+ * loads the library, held until the process exits). */
+#define VAPR_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* vapr_cost_grad for callers that cannot allocate device memory while they
+ * run: a real-time planning or control loop whose latency budget cannot
+ * absorb cudaMalloc (which may synchronise the device), or a program whose
+ * device memory is fixed at start-up or owned by another allocator.  The
+ * paper has no counterpart; it is an addition of this library.
+ *  - Same arguments and results as vapr_cost_grad, minus the workspace: the
+ *    P and G rows live in a fixed array inside the library.  The caller
+ *    still passes (and owns) every input and output.
+ *  - Nothing is allocated: no cudaMalloc, cudaFree or allocating library
+ *    call.  The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current and caches it; make
+ *    that first call before any stream capture.
+ *  - Returns VAPR_ERR_TOO_LARGE when vapr_cost_grad_workspace_bytes(robot,
+ *    n, table) exceeds VAPR_NOALLOC_SCRATCH_BYTES (FP32 storage with 52
+ *    spheres: up to 53,773 configurations per call).
+ *  - Every call shares the one array and it keeps the last call's contents;
+ *    nothing in it needs to start at zero.  Calls whose work overlaps on the
+ *    GPU (other streams, other host threads) race on it: serialise them. */
+vapr_status vapr_cost_grad_noalloc(const vapr_robot* robot, const vapr_scene* scene,
+                                   const vapr_cost_params* params, const float* q, int64_t n,
+                                   const vapr_format_table* table, const float* dcost,
+                                   float* cost, void* dist_packed, void* jgrad_packed,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,10 @@ SIGNATURES = {
                                       ctypes.POINTER(vapr_cost_params), _P, _i64,
                                       ctypes.POINTER(vapr_format_table), _P, _P, _P, _P, _P,
                                       ctypes.c_size_t, _P]),
+    "vapr_cost_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
+                                              ctypes.POINTER(vapr_cost_params), _P, _i64,
+                                              ctypes.POINTER(vapr_format_table), _P, _P, _P, _P,
+                                              _P]),
 }
 
 _lib = None
@@ -292,3 +296,19 @@ def vapr_cost_grad(robot: DeviceRobot, scene: DeviceScene, params, q, n, table, 
                                   _ptr(q), n, ctypes.byref(ct), _ptr(dcost), _ptr(cost),
                                   _ptr(dist_packed), _ptr(jgrad_packed), _ptr(workspace),
                                   nbytes, _stream(stream)), "vapr_cost_grad")
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20  # VAPR_NOALLOC_SCRATCH_BYTES
+
+
+def vapr_cost_grad_noalloc(robot: DeviceRobot, scene: DeviceScene, params, q, n, table, dcost,
+                           cost, dist_packed, jgrad_packed, stream=None):
+    """vapr_cost_grad without a workspace argument: for callers that cannot
+    allocate device memory while they run (see include/vapr.h)."""
+    ct = to_c_table(table)
+    cp = params if isinstance(params, vapr_cost_params) else cost_params(params)
+    _check(_load().vapr_cost_grad_noalloc(ctypes.byref(robot.c), ctypes.byref(scene.c),
+                                          ctypes.byref(cp), _ptr(q), n, ctypes.byref(ct),
+                                          _ptr(dcost), _ptr(cost), _ptr(dist_packed),
+                                          _ptr(jgrad_packed), _stream(stream)),
+           "vapr_cost_grad_noalloc")
