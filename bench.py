@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2310_07854_gb300 import formats as F  # noqa: E402
+from paper_2310_07854_gb300 import replicas  # noqa: E402
 from paper_2310_07854_gb300 import synth  # noqa: E402
 
 WORKLOAD = "particle_32768"
@@ -50,13 +51,6 @@ def parse_args():
     ap.add_argument("--configs", type=int, default=0,
                     help="override the batch size (configurations per GPU)")
     return ap.parse_args()
-
-
-def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
 
 
 def measured_peaks():
@@ -89,7 +83,7 @@ def cpu_baseline(workload_name: str, seconds: float) -> dict:
 
 
 def run_reference(args):
-    world, rank, _ = dist_env()
+    world, rank, _ = replicas.dist_env()
     if rank != 0:
         return
     cb = cpu_baseline(args.workload, max(args.cpu_seconds, 5.0))
@@ -218,7 +212,7 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    world, rank, local = dist_env()
+    world, rank, local = replicas.dist_env()
     import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU fallback)")
@@ -236,8 +230,7 @@ def main():
     if args.configs:
         w.q = synth.make_q(500, args.configs)
         w.n_traj = max(1, args.configs // w.horizon)
-    if rank:  # weak scaling: every rank evaluates its own batch of the same size
-        w.q = synth.make_q(1000 + rank, w.n)
+    w.q = replicas.rank_batch(w, rank)  # weak scaling: each rank its own batch
     n = w.n
     q = torch.as_tensor(w.q, device="cuda")
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
@@ -252,11 +245,7 @@ def main():
             pg.barrier()
 
     def max_over_ranks(x):
-        if not pg:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, pg, "cuda")
 
     peaks, peak_kind = measured_peaks()
     barrier()
@@ -267,8 +256,8 @@ def main():
     clocks = clk.summary()
     t32 = max_over_ranks(sum(per32["step"]))
     tv = max_over_ranks(sum(perv["step"]))
-    value = world * n * args.steps / (t32 / 1000.0)
-    value_v = world * n * args.steps / (tv / 1000.0)
+    value = replicas.job_throughput(world, n, args.steps, t32 / 1000.0)
+    value_v = replicas.job_throughput(world, n, args.steps, tv / 1000.0)
 
     # error of the VaPr table against the FP32 path (decoded by the CUDA unpacker)
     def decoded(ev):
