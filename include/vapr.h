@@ -213,6 +213,62 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
                            void* dist_packed, void* jgrad_packed, void* workspace,
                            size_t workspace_bytes, void* stream);
 
+/* ---- many uneven problems in one persistent launch ------------------------ */
+/* One planning problem of an uneven batch (device pointers, as for
+ * vapr_cost_grad): its own arm tables, obstacles, parameters,
+ * configurations and outputs.  Configuration counts, horizons and cuboid
+ * counts may all differ between problems; the format table is shared. */
+typedef struct {
+  vapr_robot robot;
+  vapr_scene scene;
+  vapr_cost_params params;
+  const float* q;        /* [n][J] */
+  int64_t n;             /* configurations: trajectories x horizon */
+  const float* dcost;    /* NULL (= 1) or [n] */
+  float* cost;           /* [n] */
+  void* dist_packed;     /* NULL or [n] rows of S values (table->dist) */
+  void* jgrad_packed;    /* [n] rows of J values (table->jgrad) */
+  int32_t deferred;      /* 0: ready at plan time; 1: waits for vapr_batched_publish */
+  int32_t reserved;      /* 0 */
+} vapr_problem;
+
+typedef struct {
+  int32_t tile;          /* configurations per work item: 32, 64, 128 or 256 */
+  int32_t wait_limit_us; /* bound on the wait for a deferred problem; 0 = 1 s */
+} vapr_batch_tuning;
+
+/* Opaque host-side handle of a plan (filled by vapr_batched_plan). */
+typedef struct {
+  uint64_t opaque[160];
+} vapr_batch_plan;
+
+/* Device bytes of the plan of this batch: problem descriptors, the work
+ * list, per-problem ready words, a work counter and one scratch slice per
+ * resident block for the packed P and G rows of a tile.  0 on a bad argument. */
+size_t vapr_batched_plan_bytes(const vapr_problem* problems, int32_t n_problems,
+                               const vapr_format_table* table, const vapr_batch_tuning* tuning);
+
+/* Builds the plan into plan_dev (device, 256-byte aligned, at least
+ * vapr_batched_plan_bytes) and fills the host handle.  problems is a HOST
+ * array.  Work items are (problem, tile of configurations) pairs, ordered
+ * by estimated cost, longest first.  Synchronous (it copies the descriptors
+ * to the device); call it once per batch shape, outside stream capture. */
+vapr_status vapr_batched_plan(const vapr_problem* problems, int32_t n_problems,
+                              const vapr_format_table* table, const vapr_batch_tuning* tuning,
+                              void* plan_dev, size_t plan_bytes, vapr_batch_plan* plan);
+
+/* Marks a deferred problem ready (a device write on `stream`). */
+vapr_status vapr_batched_publish(const vapr_batch_plan* plan, int32_t problem, void* stream);
+
+/* Evaluates every problem of the plan: one persistent launch in which each
+ * block claims work items from the counter and runs FK, the collision cost
+ * and the backward pass on the tile (results equal vapr_cost_grad per
+ * problem).  Enqueues a reset of the counter and of *dev_status, then the
+ * launch; both are stream work.  dev_status: device int32 that ends as 0, or
+ * VAPR_ERR_TIMEOUT when a deferred problem was not published within the
+ * wait limit (its items are then skipped and the others still run). */
+vapr_status vapr_batched_eval(const vapr_batch_plan* plan, int32_t* dev_status, void* stream);
+
 /* ---- the whole step without allocation ------------------------------------ */
 /* Size of the library's fixed device scratch array (64 MiB per GPU that
  * loads the library, held until the process exits). */

@@ -68,6 +68,22 @@ class vapr_cost_params(ctypes.Structure):
                 ("w_coll", ctypes.c_float), ("w_self", ctypes.c_float)]
 
 
+class vapr_problem(ctypes.Structure):
+    _fields_ = [("robot", vapr_robot), ("scene", vapr_scene), ("params", vapr_cost_params),
+                ("q", ctypes.c_void_p), ("n", ctypes.c_int64), ("dcost", ctypes.c_void_p),
+                ("cost", ctypes.c_void_p), ("dist_packed", ctypes.c_void_p),
+                ("jgrad_packed", ctypes.c_void_p), ("deferred", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class vapr_batch_tuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
+
+
+class vapr_batch_plan(ctypes.Structure):
+    _fields_ = [("opaque", ctypes.c_uint64 * 160)]
+
+
 # Every exported symbol, with (restype, argtypes).
 _P = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -94,6 +110,15 @@ SIGNATURES = {
                                       ctypes.POINTER(vapr_cost_params), _P, _i64,
                                       ctypes.POINTER(vapr_format_table), _P, _P, _P, _P, _P,
                                       ctypes.c_size_t, _P]),
+    "vapr_batched_plan_bytes": (ctypes.c_size_t, [ctypes.POINTER(vapr_problem), ctypes.c_int32,
+                                                  ctypes.POINTER(vapr_format_table),
+                                                  ctypes.POINTER(vapr_batch_tuning)]),
+    "vapr_batched_plan": (ctypes.c_int, [ctypes.POINTER(vapr_problem), ctypes.c_int32,
+                                         ctypes.POINTER(vapr_format_table),
+                                         ctypes.POINTER(vapr_batch_tuning), _P, ctypes.c_size_t,
+                                         ctypes.POINTER(vapr_batch_plan)]),
+    "vapr_batched_publish": (ctypes.c_int, [ctypes.POINTER(vapr_batch_plan), ctypes.c_int32, _P]),
+    "vapr_batched_eval": (ctypes.c_int, [ctypes.POINTER(vapr_batch_plan), _P, _P]),
     "vapr_cost_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
                                               ctypes.POINTER(vapr_cost_params), _P, _i64,
                                               ctypes.POINTER(vapr_format_table), _P, _P, _P, _P,
@@ -312,3 +337,27 @@ def vapr_cost_grad_noalloc(robot: DeviceRobot, scene: DeviceScene, params, q, n,
                                           _ptr(dcost), _ptr(cost), _ptr(dist_packed),
                                           _ptr(jgrad_packed), _stream(stream)),
            "vapr_cost_grad_noalloc")
+
+
+def vapr_batched_plan_bytes(problems, table, tuning) -> int:
+    ct = to_c_table(table)
+    return int(_load().vapr_batched_plan_bytes(problems, len(problems), ctypes.byref(ct),
+                                               ctypes.byref(tuning)))
+
+
+def vapr_batched_plan(problems, table, tuning, plan_dev, plan: "vapr_batch_plan"):
+    ct = to_c_table(table)
+    nbytes = plan_dev.numel() if hasattr(plan_dev, "numel") else int(plan_dev[1])
+    _check(_load().vapr_batched_plan(problems, len(problems), ctypes.byref(ct),
+                                     ctypes.byref(tuning), _ptr(plan_dev), nbytes,
+                                     ctypes.byref(plan)), "vapr_batched_plan")
+
+
+def vapr_batched_publish(plan: "vapr_batch_plan", problem: int, stream=None):
+    _check(_load().vapr_batched_publish(ctypes.byref(plan), problem, _stream(stream)),
+           "vapr_batched_publish")
+
+
+def vapr_batched_eval(plan: "vapr_batch_plan", dev_status, stream=None):
+    _check(_load().vapr_batched_eval(ctypes.byref(plan), _ptr(dev_status), _stream(stream)),
+           "vapr_batched_eval")

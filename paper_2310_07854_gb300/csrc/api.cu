@@ -11,13 +11,13 @@ namespace vapr {
 
 static thread_local int g_last_cuda_error = 0;
 
-static vapr_status cuda_status(cudaError_t e) {
+vapr_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return VAPR_OK;
   g_last_cuda_error = (int)e;
   return VAPR_ERR_CUDA;
 }
 
-static bool fmt_ok(vapr_format f) {
+bool fmt_ok(vapr_format f) {
   const int E = f.exp_bits, M = f.man_bits, fl = f.flags;
   if (f.reserved != 0) return false;
   if (E < 2 || E > 8 || M < 1 || M > 23) return false;
@@ -125,7 +125,7 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
   return blocks;
 }
 
-static size_t row_bytes(int64_t row_len, vapr_format f) {
+size_t row_bytes(int64_t row_len, vapr_format f) {
   if (row_len <= 0 || !fmt_ok(f)) return 0;
   const int64_t k = 32 / (1 + f.exp_bits + f.man_bits);
   const int64_t words = (row_len + k - 1) / k;
@@ -185,7 +185,7 @@ cudaError_t launch_unpack(Packed src, int64_t rows, int64_t row_len, float* dst,
   return cudaGetLastError();
 }
 
-static vapr_status check_robot(const vapr_robot* r, RobotArgs* out) {
+vapr_status check_robot(const vapr_robot* r, RobotArgs* out) {
   if (!r) return VAPR_ERR_INVALID_ARG;
   if (r->n_joints < 1 || r->n_joints > VAPR_MAX_JOINTS) return VAPR_ERR_INVALID_ARG;
   if (r->n_spheres < 1 || r->n_spheres > VAPR_MAX_SPHERES) return VAPR_ERR_INVALID_ARG;
@@ -205,7 +205,7 @@ static vapr_status check_robot(const vapr_robot* r, RobotArgs* out) {
   return VAPR_OK;
 }
 
-static vapr_status check_table(const vapr_format_table* t) {
+vapr_status check_table(const vapr_format_table* t) {
   if (!t) return VAPR_ERR_INVALID_ARG;
   if (!fmt_ok(t->pos) || !fmt_ok(t->dist) || !fmt_ok(t->grad) || !fmt_ok(t->jgrad) ||
       !fmt_ok(t->xform))

@@ -33,6 +33,12 @@ struct Packed {
 };
 
 DevFmt make_dev_fmt(vapr_format f);
+// Argument checks shared by the entry points (api.cu).
+bool fmt_ok(vapr_format f);
+size_t row_bytes(int64_t row_len, vapr_format f);  // packed row, padded to 16 B
+vapr_status check_robot(const vapr_robot* r, RobotArgs* out);
+vapr_status check_table(const vapr_format_table* t);
+vapr_status cuda_status(cudaError_t e);           // records the error for vapr_last_cuda_error
 int sm_count();  // SMs of the current device (cached per device)
 // Resident blocks per SM of `fn` at `threads` and `smem` dynamic bytes on the
 // current device.  The first call for a (kernel, device, smem) also raises

@@ -1,0 +1,588 @@
+// The three stages of the path as block-, warp- and thread-level device
+// functions, shared by the single-problem kernels (fk.cu, collision.cu,
+// backward.cu) and the uneven multi-problem kernel (batched.cu), so every
+// entry point runs the same arithmetic on a configuration.
+//
+//   FK         (Sec. II-B; iteration step 2 of Sec. III-B):
+//              T_0 = I, T_j = T_{j-1} F_j Rz(q_j), c_s = T_link(s) [p_s; 1]
+//   collision  (iteration steps 3-4): box distance d = |max(u,0)| +
+//              min(max u, 0), u = |R^T (c - t)| - h;
+//              D_s = sum_o max(0, r_s + eta - d_o(c_s));
+//              P_ij = max(0, r_i + r_j + eta_s - |c_i - c_j|);
+//              C = w_c sum D + w_s sum P;  G = dC/dc
+//   backward   (iteration step 5): J_j = a_j . M_{>=j} - b_j . F_{>=j},
+//              F = sum G_s, M = sum c_s x G_s, b_j = a_j x o_j
+#pragma once
+
+#include "common.cuh"
+
+namespace vapr {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Hands out 16-byte-aligned slices of a buffer in a fixed order.  With a
+// null base it only counts bytes, so the host sizes shared memory with the
+// same code the device uses to carve it.
+struct Bump {
+  char* base;
+  size_t off;
+  __host__ __device__ explicit Bump(void* b) : base((char*)b), off(0) {}
+  template <typename T>
+  __host__ __device__ T* take(size_t n) {
+    off = (off + 15) & ~(size_t)15;
+    T* r = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return r;
+  }
+  __host__ __device__ size_t bytes() const { return (off + 15) & ~(size_t)15; }
+};
+
+// ------------------------------------------------------------ robot tables
+struct RobotSm {
+  float4* F;    // [3J] rows of F_j: (R_d0, R_d1, R_d2, t_d)
+  float4* sph;  // [S] (p, r)
+  int* link0;   // [S] 0-based link, clamped into range
+  int* order;   // [S] spheres grouped by link (stable)
+  int* start;   // [J+1] first slot of each link in order
+};
+
+__host__ __device__ inline void carve_robot(Bump& b, int J, int S, RobotSm& r) {
+  r.F = b.take<float4>(3 * J);
+  r.sph = b.take<float4>(S);
+  r.link0 = b.take<int>(S);
+  r.order = b.take<int>(S);
+  r.start = b.take<int>(J + 1);
+}
+
+// Block-cooperative; the caller synchronises the block afterwards.
+__device__ inline void load_robot(const RobotArgs& a, const RobotSm& r) {
+  const int J = a.J, S = a.S;
+  for (int i = threadIdx.x; i < 3 * J; i += blockDim.x) {
+    const int j = i / 3, d = i - 3 * j;
+    const float* F = a.joint_fixed + 12 * j;
+    r.F[i] = make_float4(F[3 * d], F[3 * d + 1], F[3 * d + 2], F[9 + d]);
+  }
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    r.sph[s] = reinterpret_cast<const float4*>(a.sphere_local)[s];
+    r.link0[s] = clampi(a.sphere_link[s], 1, J) - 1;
+  }
+  if (threadIdx.x == 0) {  // stable counting sort of the spheres by link
+    for (int j = 0; j <= J; ++j) r.start[j] = 0;
+    for (int s = 0; s < S; ++s) ++r.start[clampi(a.sphere_link[s], 1, J)];
+    for (int j = 1; j <= J; ++j) r.start[j] += r.start[j - 1];
+    for (int s = S - 1; s >= 0; --s) r.order[--r.start[clampi(a.sphere_link[s], 1, J)]] = s;
+    for (int j = 0; j < J; ++j) r.start[j] = r.start[j + 1];
+    r.start[J] = S;
+  }
+}
+
+// ------------------------------------------------------------ FK (thread)
+// The joint chain of one configuration into myT: 3 float4 per joint, rows
+// (R_d0, R_d1, R_d2, t_d).
+__device__ __forceinline__ void fk_chain(const RobotSm& r, int J, const float* q, float4* myT) {
+  float R[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  float t[3] = {0.f, 0.f, 0.f};
+  for (int j = 0; j < J; ++j) {
+    const float4 f0 = r.F[3 * j], f1 = r.F[3 * j + 1], f2 = r.F[3 * j + 2];
+    float B[3][3], tb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // T_{j-1} F_j
+      B[k][0] = fmaf(R[k][0], f0.x, fmaf(R[k][1], f1.x, R[k][2] * f2.x));
+      B[k][1] = fmaf(R[k][0], f0.y, fmaf(R[k][1], f1.y, R[k][2] * f2.y));
+      B[k][2] = fmaf(R[k][0], f0.z, fmaf(R[k][1], f1.z, R[k][2] * f2.z));
+      tb[k] = fmaf(R[k][0], f0.w, fmaf(R[k][1], f1.w, fmaf(R[k][2], f2.w, t[k])));
+    }
+    float sn, cs;
+    sincosf(q[j], &sn, &cs);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // ... Rz(q_j)
+      R[k][0] = fmaf(cs, B[k][0], sn * B[k][1]);
+      R[k][1] = fmaf(cs, B[k][1], -sn * B[k][0]);
+      R[k][2] = B[k][2];
+      t[k] = tb[k];
+      myT[3 * j + k] = make_float4(R[k][0], R[k][1], R[k][2], t[k]);
+    }
+  }
+}
+
+// Packed sphere-centre row of one configuration from its transforms T;
+// lanes take the row's 32-bit words (padding words written as zero).
+template <int K>
+__device__ __forceinline__ void fk_store_pos(const RobotSm& r, int S, const float4* T,
+                                             uint32_t* out, int words, const DevFmt& f, int lane) {
+  const int nv = 3 * S;
+  for (int w = lane; w < words; w += 32)
+    out[w] = pack_word_t<K>(w, nv, f, [&](int i) {
+      const int s = i / 3, d = i - 3 * s;
+      const float4 row = T[3 * r.link0[s] + d];
+      const float4 p = r.sph[s];
+      return fmaf(row.x, p.x, fmaf(row.y, p.y, fmaf(row.z, p.z, row.w)));
+    });
+}
+
+// Packed link-transform row (element e of T_j is value 12 j + e).
+template <int K>
+__device__ __forceinline__ void fk_store_xform(int J, const float4* T, uint32_t* out, int words,
+                                               const DevFmt& f, int lane) {
+  const int nv = 12 * J;
+  for (int w = lane; w < words; w += 32)
+    out[w] = pack_word_t<K>(w, nv, f, [&](int i) {
+      const int j = i / 12, e = i - 12 * j;
+      const int d = e < 9 ? e / 3 : e - 9;
+      const int col = e < 9 ? e - 3 * d : 3;
+      const float4 row = T[3 * j + d];
+      return col == 0 ? row.x : col == 1 ? row.y : col == 2 ? row.z : row.w;
+    });
+}
+
+// ------------------------------------------------------- collision (warp)
+constexpr int QCAP = 64;         // warp queue of (sphere, cuboid) pairs
+constexpr int CHUNK = 64;        // cuboids per culling pass
+constexpr float SLACK = 1e-4f;   // metres: covers float32 rounding of the culls
+
+struct SceneSm {
+  float4* cubA;  // [O][3]: (column k of R, t_k), k = 0..2
+  float4* cubH;  // [O]: (half extents, unused)
+  float4* cubC;  // [O]: (centre, bounding radius + eta + SLACK)
+  uint2* pairs;  // [NP]: (i | j << 16, bits of r_i + r_j + eta_s)
+};
+
+__host__ __device__ inline void carve_scene(Bump& b, int O, int NP, SceneSm& s) {
+  s.cubA = b.take<float4>(3 * O);
+  s.cubH = b.take<float4>(O);
+  s.cubC = b.take<float4>(O);
+  s.pairs = b.take<uint2>(NP);
+}
+
+__device__ inline void load_scene(const RobotArgs& r, const SceneArgs& sc, float eta, float eta_s,
+                                  const SceneSm& m) {
+  const int O = sc.O, S = r.S;
+  for (int o = threadIdx.x; o < O; o += blockDim.x) {
+    const float* p = sc.pose + 12 * o;
+    const float hx = sc.half[3 * o], hy = sc.half[3 * o + 1], hz = sc.half[3 * o + 2];
+    m.cubA[3 * o + 0] = make_float4(p[0], p[3], p[6], p[9]);
+    m.cubA[3 * o + 1] = make_float4(p[1], p[4], p[7], p[10]);
+    m.cubA[3 * o + 2] = make_float4(p[2], p[5], p[8], p[11]);
+    m.cubH[o] = make_float4(hx, hy, hz, 0.f);
+    m.cubC[o] = make_float4(p[9], p[10], p[11], sqrtf(hx * hx + hy * hy + hz * hz) + eta + SLACK);
+  }
+  for (int p = threadIdx.x; p < r.NP; p += blockDim.x) {
+    const int i = clampi(r.pairs[2 * p], 0, S - 1), j = clampi(r.pairs[2 * p + 1], 0, S - 1);
+    m.pairs[p] = make_uint2((uint32_t)i | ((uint32_t)j << 16),
+                            __float_as_uint(r.sphere_local[4 * i + 3] + r.sphere_local[4 * j + 3] +
+                                            eta_s));
+  }
+}
+
+// One warp's working set for one configuration.
+struct CollWarp {
+  float4* P;        // [S] (x, y, z, r)
+  float4* acc;      // [S] (D, gx, gy, gz)
+  float4* lb;       // [J] link bounding sphere (centre, radius)
+  uint32_t* queue;  // [QCAP] sphere | cuboid << 16
+  int* ccount;      // [J]
+  uint16_t* cand;   // [J][CHUNK] candidate cuboids of each link
+};
+
+__host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp& w) {
+  w.P = b.take<float4>(S);
+  w.acc = b.take<float4>(S);
+  w.lb = b.take<float4>(J);
+  w.queue = b.take<uint32_t>(QCAP);
+  w.ccount = b.take<int>(J);
+  w.cand = b.take<uint16_t>((size_t)J * CHUNK);
+}
+
+// Radii into P[].w and zero accumulators (once per robot).
+__device__ __forceinline__ void init_coll_warp(const RobotArgs& r, const CollWarp& w, int lane) {
+  for (int s = lane; s < r.S; s += 32) {
+    w.P[s] = make_float4(0.f, 0.f, 0.f, r.sphere_local[4 * s + 3]);
+    w.acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Exact narrow phase of queue entries 0..cnt-1 (one per lane) and their
+// accumulation, rank by rank, into acc: entries of a sphere are contiguous
+// and in cuboid order, so each sphere sums its contributions sequentially.
+__device__ __forceinline__ void coll_flush(const SceneSm& m, const CollWarp& w, int cnt, float eta,
+                                           float w_c, int lane) {
+  const bool have = lane < cnt;
+  const uint32_t e = have ? w.queue[lane] : 0xffffffffu;
+  const int s = (int)(e & 0xffffu), o = (int)(e >> 16);
+  float dD = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  if (have) {
+    const float4 c = w.P[s];
+    const float4 A0 = m.cubA[3 * o], A1 = m.cubA[3 * o + 1], A2 = m.cubA[3 * o + 2];
+    const float4 H = m.cubH[o];
+    const float dx = c.x - A0.w, dy = c.y - A1.w, dz = c.z - A2.w;
+    const float x0 = fmaf(A0.x, dx, fmaf(A0.y, dy, A0.z * dz));
+    const float x1 = fmaf(A1.x, dx, fmaf(A1.y, dy, A1.z * dz));
+    const float x2 = fmaf(A2.x, dx, fmaf(A2.y, dy, A2.z * dz));
+    const float u0 = fabsf(x0) - H.x, u1 = fabsf(x1) - H.y, u2 = fabsf(x2) - H.z;
+    const float v0 = fmaxf(u0, 0.f), v1 = fmaxf(u1, 0.f), v2 = fmaxf(u2, 0.f);
+    const float n2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+    const bool outside = u0 > 0.f || u1 > 0.f || u2 > 0.f;
+    // inside: the face of the largest u (lowest axis on ties)
+    const int k = (u0 >= u1 && u0 >= u2) ? 0 : (u1 >= u2 ? 1 : 2);
+    const float umax = fmaxf(u0, fmaxf(u1, u2));
+    const float rs = n2 > 0.f ? rsqrtf(n2) : 0.f;  // 1/|max(u,0)|
+    const float d = outside ? n2 * rs : umax;
+    const float pen = c.w + eta - d;
+    if (pen > 0.f) {
+      const float inv = outside ? rs : 0.f;
+      const float s0 = x0 >= 0.f ? 1.f : -1.f, s1 = x1 >= 0.f ? 1.f : -1.f,
+                  s2 = x2 >= 0.f ? 1.f : -1.f;
+      const float l0 = outside ? s0 * v0 * inv : (k == 0 ? s0 : 0.f);
+      const float l1 = outside ? s1 * v1 * inv : (k == 1 ? s1 : 0.f);
+      const float l2 = outside ? s2 * v2 * inv : (k == 2 ? s2 : 0.f);
+      dD = pen;  // gradient of the hinge: -grad d, scaled by w_coll
+      gx = -w_c * fmaf(A0.x, l0, fmaf(A1.x, l1, A2.x * l2));
+      gy = -w_c * fmaf(A0.y, l0, fmaf(A1.y, l1, A2.y * l2));
+      gz = -w_c * fmaf(A0.z, l0, fmaf(A1.z, l1, A2.z * l2));
+    }
+  }
+  const int prev = __shfl_up_sync(FULL_MASK, s, 1);
+  const bool head = lane == 0 || !have || s != prev;
+  const unsigned heads = __ballot_sync(FULL_MASK, head);
+  const int rank = lane - (31 - __clz(heads & (FULL_MASK >> (31 - lane))));
+  const int rounds = __reduce_max_sync(FULL_MASK, have ? rank : 0);
+  for (int r = 0; r <= rounds; ++r) {
+    if (have && rank == r) {
+      float4 a = w.acc[s];
+      a.x += dD;
+      a.y += gx;
+      a.z += gy;
+      a.w += gz;
+      w.acc[s] = a;
+    }
+    __syncwarp();
+  }
+}
+
+struct CollOut {
+  float* cost;        // this configuration's cost, or null
+  uint32_t* dist;     // packed D row, or null
+  int dist_words;
+  uint32_t* grad;     // packed G row, or null
+  int grad_words;
+};
+
+// The whole collision stage of one configuration by one warp: P row in,
+// cost, D and G rows out.  Culling is conservative (see collision.cu).
+// COHERENT reads the P row with loads that see writes made earlier in the
+// same kernel (the fused multi-problem kernel); otherwise through the
+// read-only cache.
+template <bool COHERENT = false>
+__device__ __forceinline__ void collision_config(const RobotArgs& r, int O, const RobotSm& rb,
+                                                 const SceneSm& m, const CollWarp& w,
+                                                 const uint32_t* prow, const DevFmt& fP,
+                                                 const DevFmt& fD, const DevFmt& fG, float eta,
+                                                 float w_c, float w_s, const CollOut& out,
+                                                 int lane) {
+  const int J = r.J, S = r.S, NP = r.NP;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  // ---- 1. sphere centres (one word per lane)
+  {
+    const int nv = 3 * S;
+    dispatch_kind(fP.kind, [&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      const int kw = per_word<K>(fP);
+      const int nw = (nv + kw - 1) / kw;
+      for (int wd = lane; wd < nw; wd += 32) {
+        const uint32_t word = COHERENT ? __ldcg(prow + wd) : __ldg(prow + wd);
+        unpack_word_t<K>(word, wd, nv, fP, [&](int i, float x) {
+          const int s = i / 3;
+          reinterpret_cast<float*>(w.P + s)[i - 3 * s] = x;
+        });
+      }
+    });
+  }
+  __syncwarp();
+  // ---- 2. link bounding spheres centred on the middle sphere of the link;
+  //      radius = max |c_s - centre| + r_s (integer atomicMax on float bits)
+  if (lane < J) {
+    const int b = rb.start[lane], e = rb.start[lane + 1];
+    const float4 ctr = e > b ? w.P[rb.order[b + (e - b) / 2]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    w.lb[lane] = make_float4(ctr.x, ctr.y, ctr.z, e > b ? 0.f : -1.f);
+  }
+  __syncwarp();
+  for (int s = lane; s < S; s += 32) {
+    const float4 p = w.P[s];
+    const float4 b = w.lb[rb.link0[s]];
+    const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rad = (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f) + p.w + SLACK;
+    atomicMax(reinterpret_cast<int*>(w.lb + rb.link0[s]) + 3, __float_as_int(rad));
+  }
+  __syncwarp();
+  // ---- 3. environment: cull, compact, evaluate (CHUNK cuboids per pass)
+  for (int base = 0; base < O; base += CHUNK) {
+    const int o0 = base + lane, o1 = base + 32 + lane;
+    const float4 C0 = o0 < O ? m.cubC[o0] : make_float4(0.f, 0.f, 0.f, -1e30f);
+    const float4 C1 = o1 < O ? m.cubC[o1] : make_float4(0.f, 0.f, 0.f, -1e30f);
+    for (int L = 0; L < J; ++L) {
+      const float4 b = w.lb[L];
+      bool n0 = false, n1 = false;
+      if (b.w >= 0.f) {
+        const float ax = b.x - C0.x, ay = b.y - C0.y, az = b.z - C0.z;
+        const float t0 = b.w + C0.w;
+        n0 = C0.w > 0.f && fmaf(ax, ax, fmaf(ay, ay, az * az)) < t0 * t0;
+        const float bx = b.x - C1.x, by = b.y - C1.y, bz = b.z - C1.z;
+        const float t1 = b.w + C1.w;
+        n1 = C1.w > 0.f && fmaf(bx, bx, fmaf(by, by, bz * bz)) < t1 * t1;
+      }
+      const unsigned m0 = __ballot_sync(FULL_MASK, n0), m1 = __ballot_sync(FULL_MASK, n1);
+      uint16_t* cl = w.cand + L * CHUNK;
+      if (n0) cl[__popc(m0 & lt_mask)] = (uint16_t)o0;
+      if (n1) cl[__popc(m0) + __popc(m1 & lt_mask)] = (uint16_t)o1;
+      if (lane == 0) w.ccount[L] = __popc(m0) + __popc(m1);
+    }
+    __syncwarp();
+    int qn = 0;
+    for (int L = 0; L < J; ++L) {  // (sphere of L, candidate): sphere-major, dense over lanes
+      const int cl_n = w.ccount[L];
+      const int s0 = rb.start[L], ns = rb.start[L + 1] - s0;
+      const int total = cl_n * ns;
+      if (total == 0) continue;
+      const float rcp = 1.0f / (float)cl_n;
+      const uint16_t* cl = w.cand + L * CHUNK;
+      for (int t = 0; t < total; t += 32) {
+        const int idx = t + lane;
+        bool nr = false;
+        int s = 0, o = 0;
+        if (idx < total) {
+          int js = __float2int_rd(((float)idx + 0.5f) * rcp);  // idx / cl_n
+          int jc = idx - js * cl_n;
+          if (jc >= cl_n) { ++js; jc -= cl_n; }  // exact quotient whatever the rounding
+          if (jc < 0) { --js; jc += cl_n; }
+          s = rb.order[s0 + js];
+          o = cl[jc];
+          const float4 p = w.P[s];
+          const float4 C = m.cubC[o];
+          const float dx = p.x - C.x, dy = p.y - C.y, dz = p.z - C.z;
+          const float thr = p.w + C.w;
+          nr = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < thr * thr;
+        }
+        const unsigned bal = __ballot_sync(FULL_MASK, nr);
+        if (nr) w.queue[qn + __popc(bal & lt_mask)] = (uint32_t)s | ((uint32_t)o << 16);
+        qn += __popc(bal);
+        if (qn >= 32) {
+          __syncwarp();
+          coll_flush(m, w, 32, eta, w_c, lane);
+          const int rest = qn - 32;
+          const uint32_t moved = lane < rest ? w.queue[32 + lane] : 0u;
+          __syncwarp();
+          if (lane < rest) w.queue[lane] = moved;
+          qn = rest;
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+    if (qn > 0) coll_flush(m, w, qn, eta, w_c, lane);  // runs never span passes
+    __syncwarp();
+  }
+  // ---- 4. self-collision over the pair list
+  float selfsum = 0.f;
+  for (int pb = 0; pb < NP; pb += 32) {
+    const int p = pb + lane;
+    bool act = false;
+    float pen = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+    int i = 0, j = 0;
+    if (p < NP) {
+      const uint2 pr = m.pairs[p];
+      i = (int)(pr.x & 0xffffu);
+      j = (int)(pr.x >> 16);
+      const float4 ci = w.P[i], cj = w.P[j];
+      const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float thr = __uint_as_float(pr.y);
+      if (d2 < thr * thr) {
+        const float rs = d2 > 0.f ? rsqrtf(d2) : 0.f;
+        pen = thr - d2 * rs;
+        act = pen > 0.f;
+        const float inv = w_s * rs;  // 0 at zero distance: no gradient
+        ux = dx * inv;
+        uy = dy * inv;
+        uz = dz * inv;
+      }
+    }
+    unsigned am = __ballot_sync(FULL_MASK, act);
+    if (act) selfsum += pen;
+    while (am) {  // active pairs are rare: apply them one lane at a time, in pair order
+      const int l = __ffs(am) - 1;
+      if (lane == l) {
+        float4 vi = w.acc[i];
+        vi.y -= ux;
+        vi.z -= uy;
+        vi.w -= uz;
+        w.acc[i] = vi;
+        float4 vj = w.acc[j];
+        vj.y += ux;
+        vj.z += uy;
+        vj.w += uz;
+        w.acc[j] = vj;
+      }
+      __syncwarp();
+      am &= am - 1u;
+    }
+  }
+  __syncwarp();
+  // ---- 5. cost and packed outputs (one word per lane), then reset acc
+  float local = 0.f;
+  for (int s = lane; s < S; s += 32) local += w.acc[s].x;
+  local = w_c * local + w_s * selfsum;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULL_MASK, local, off);
+  if (out.cost && lane == 0) *out.cost = local;
+  if (out.dist) {
+    dispatch_kind(fD.kind, [&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      for (int wd = lane; wd < out.dist_words; wd += 32)
+        out.dist[wd] = pack_word_t<K>(wd, S, fD, [&](int i) { return w.acc[i].x; });
+    });
+  }
+  if (out.grad) {
+    const int nv = 3 * S;
+    dispatch_kind(fG.kind, [&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      for (int wd = lane; wd < out.grad_words; wd += 32)
+        out.grad[wd] = pack_word_t<K>(wd, nv, fG, [&](int i) {
+          const int s = i / 3;
+          return reinterpret_cast<const float*>(w.acc + s)[1 + i - 3 * s];
+        });
+    });
+  }
+  __syncwarp();
+  for (int s = lane; s < S; s += 32) w.acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncwarp();
+}
+
+// ------------------------------------------------------- backward (thread)
+// Streams the words of one packed row, caching the current 16-byte chunk.
+// Where the row lives: shared memory, global through the read-only cache,
+// or global written earlier in the same kernel (coherent L2 loads).
+enum RowSrc : int { ROW_SHARED = 0, ROW_GLOBAL_RO = 1, ROW_GLOBAL_COHERENT = 2 };
+
+template <int SRC>
+struct RowReader {
+  const uint8_t* row;
+  int chunk = -1;
+  uint4 v;
+  __device__ __forceinline__ uint32_t word(int w) {
+    const int c = w >> 2;
+    if (c != chunk) {
+      const uint4* p = reinterpret_cast<const uint4*>(row) + c;
+      if constexpr (SRC == ROW_GLOBAL_RO) v = __ldg(p);
+      else if constexpr (SRC == ROW_GLOBAL_COHERENT) v = __ldcg(p);
+      else v = *p;
+      chunk = c;
+    }
+    const int q = w & 3;
+    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+  }
+  __device__ __forceinline__ float value(int i, const DevFmt& f) {  // runtime format
+    const int w = i / f.k;
+    return unpack_slot(word(w), i - w * f.k, f);
+  }
+  template <int K>
+  __device__ __forceinline__ float value_k(int i, const DevFmt& f) {  // compile-time format
+    return row_value<K>(i, f, [&](int w) { return word(w); });
+  }
+};
+
+// Joint gradient of one configuration into myK[2j+1].w (times dc).
+// live == false runs the same control flow without touching memory.
+// before_spheres() is called once, by every lane, before the first gradient
+// value is read; returning false aborts (the function returns false).
+template <int GK, int GSRC, typename Before>
+__device__ __forceinline__ bool backward_config(const RobotSm& rb, int J, bool live,
+                                                const float* q, RowReader<ROW_GLOBAL_RO>& x,
+                                                const DevFmt& fx, RowReader<GSRC>& g,
+                                                const DevFmt& fg, float dc, float4* myK,
+                                                Before before_spheres) {
+  float R[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
+  float t[3] = {0.f, 0.f, 0.f};
+  float F0 = 0.f, F1 = 0.f, F2 = 0.f, M0 = 0.f, M1 = 0.f, M2 = 0.f;
+  bool staged = false;
+  for (int j = 0; j < J; ++j) {
+    if (live) {
+      if (x.row) {  // stored transforms: element e of T_j is value 12j + e
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+          for (int l = 0; l < 3; ++l) R[k][l] = x.value(12 * j + 3 * k + l, fx);
+          t[k] = x.value(12 * j + 9 + k, fx);
+        }
+      } else {  // recompute T_j = T_{j-1} F_j Rz(q_j)
+        const float4 f0 = rb.F[3 * j], f1 = rb.F[3 * j + 1], f2 = rb.F[3 * j + 2];
+        float B[3][3], tb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          B[k][0] = fmaf(R[k][0], f0.x, fmaf(R[k][1], f1.x, R[k][2] * f2.x));
+          B[k][1] = fmaf(R[k][0], f0.y, fmaf(R[k][1], f1.y, R[k][2] * f2.y));
+          B[k][2] = fmaf(R[k][0], f0.z, fmaf(R[k][1], f1.z, R[k][2] * f2.z));
+          tb[k] = fmaf(R[k][0], f0.w, fmaf(R[k][1], f1.w, fmaf(R[k][2], f2.w, t[k])));
+        }
+        float sn, cs;
+        sincosf(q[j], &sn, &cs);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          R[k][0] = fmaf(cs, B[k][0], sn * B[k][1]);
+          R[k][1] = fmaf(cs, B[k][1], -sn * B[k][0]);
+          R[k][2] = B[k][2];
+          t[k] = tb[k];
+        }
+      }
+    }
+    // axis a_j, b_j = a_j x o_j, and the correction K_j
+    const float ax = R[0][2], ay = R[1][2], az = R[2][2];
+    const float bx = ay * t[2] - az * t[1];
+    const float by = az * t[0] - ax * t[2];
+    const float bz = ax * t[1] - ay * t[0];
+    const float K = (ax * M0 + ay * M1 + az * M2) - (bx * F0 + by * F1 + bz * F2);
+    myK[2 * j] = make_float4(ax, ay, az, K);
+    myK[2 * j + 1] = make_float4(bx, by, bz, 0.f);
+    if (!staged && rb.start[j + 1] > rb.start[j]) {
+      if (!before_spheres()) return false;
+      staged = true;
+    }
+    if (live) {  // spheres on link j: F += G, M += c x G
+      for (int idx = rb.start[j]; idx < rb.start[j + 1]; ++idx) {
+        const int s = rb.order[idx];
+        const float g0 = g.template value_k<GK>(3 * s, fg);
+        const float g1 = g.template value_k<GK>(3 * s + 1, fg);
+        const float g2 = g.template value_k<GK>(3 * s + 2, fg);
+        if (g0 == 0.f && g1 == 0.f && g2 == 0.f) continue;
+        const float4 p = rb.sph[s];
+        const float c0 = fmaf(R[0][0], p.x, fmaf(R[0][1], p.y, fmaf(R[0][2], p.z, t[0])));
+        const float c1 = fmaf(R[1][0], p.x, fmaf(R[1][1], p.y, fmaf(R[1][2], p.z, t[1])));
+        const float c2 = fmaf(R[2][0], p.x, fmaf(R[2][1], p.y, fmaf(R[2][2], p.z, t[2])));
+        F0 += g0;
+        F1 += g1;
+        F2 += g2;
+        M0 += c1 * g2 - c2 * g1;
+        M1 += c2 * g0 - c0 * g2;
+        M2 += c0 * g1 - c1 * g0;
+      }
+    }
+  }
+  if (!staged && !before_spheres()) return false;
+  for (int j = 0; j < J; ++j) {
+    const float4 ak = myK[2 * j], b = myK[2 * j + 1];
+    const float Jj = (ak.x * M0 + ak.y * M1 + ak.z * M2) - (b.x * F0 + b.y * F1 + b.z * F2) - ak.w;
+    myK[2 * j + 1].w = dc * Jj;
+  }
+  return true;
+}
+
+// Packed joint-gradient row from myK (padding words written as zero).
+__device__ __forceinline__ void backward_store(int J, const float4* myK, uint8_t* row, int64_t stride,
+                                               const DevFmt& fj) {
+  uint4* out = reinterpret_cast<uint4*>(row);
+  const int chunks = (int)(stride / 16);
+  for (int cc = 0; cc < chunks; ++cc)
+    out[cc] = pack_chunk_dyn(cc, J, fj, [&](int i) { return myK[2 * i + 1].w; });
+}
+
+}  // namespace vapr

@@ -124,3 +124,19 @@ def test_cost_grad_workspace_and_checks():
     assert lib.vapr_cost_grad(*args(1040, need)) == 3           # not 256-byte aligned
     assert lib.vapr_cost_grad(*args(None, need)) == 1
     assert lib.vapr_cost_grad(*args(1024, 0, n=0)) == 0         # n == 0: no-op
+
+
+def test_batched_argument_checks():
+    lib = B.lib()
+    byref = ctypes.byref
+    ct = B.to_c_table(F.FP32_TABLE)
+    arr = (B.vapr_problem * 1)()
+    for tile in (0, 16, 100, 512):
+        assert lib.vapr_batched_plan_bytes(arr, 1, byref(ct), byref(B.vapr_batch_tuning(tile, 0))) == 0
+    assert lib.vapr_batched_plan_bytes(arr, 0, byref(ct), byref(B.vapr_batch_tuning(128, 0))) == 0
+    plan = B.vapr_batch_plan()
+    assert lib.vapr_batched_eval(byref(plan), 256, None) == 1       # not a plan
+    assert lib.vapr_batched_eval(None, 256, None) == 1
+    assert lib.vapr_batched_publish(byref(plan), 0, None) == 1
+    assert lib.vapr_batched_plan(arr, 1, byref(ct), byref(B.vapr_batch_tuning(128, 0)),
+                                 264, 1 << 20, byref(plan)) == 3    # plan buffer misaligned

@@ -11,7 +11,8 @@ Checks, besides producing the report:
   (P on P; D on P, D; G on P, G; J on P, G, J), which is the data flow of
   the staged path;
 * a tensor's own rounding error is bounded by half a unit in the last place
-  of its format at the tensor's largest magnitude, plus the propagated error.
+  of its format at the tensor's largest magnitude, plus the propagated error,
+  plus how far the tensor exceeds the format's largest value (saturation).
 Set VAPR_REPORT_DIR to write the report as JSON.
 """
 import itertools
@@ -33,11 +34,14 @@ TENSORS = ("pos", "dist", "grad", "jgrad")
 
 
 def _half_ulp(f, mag):
-    """Half the spacing of format f just below magnitude mag."""
+    """Largest rounding error of format f on values up to magnitude mag:
+    half a spacing at mag, or the distance past the largest finite value."""
     if f == F.FP32:
         return float(np.spacing(np.float32(mag))) / 2
-    e = np.floor(np.log2(max(mag, 1e-30)))
-    return 2.0 ** (e - f.M) / 2
+    top = oracle.max_finite(f.E, f.M, f.flags)
+    e = np.floor(np.log2(max(min(mag, top), 1e-30)))
+    half = 2.0 ** (e - f.M) / 2
+    return max(half, mag - top)
 
 
 def test_vapr_sweep_1024():
