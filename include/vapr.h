@@ -136,9 +136,10 @@ int vapr_format_supported(vapr_format f);
  * row_len <= 0 or f is unsupported) */
 size_t vapr_packed_row_bytes(int64_t row_len, vapr_format f);
 
-/* Reads and clears the sticky error word of kernels with device-side waits
- * (the TMA staging wait of vapr_backward): *code receives VAPR_ERR_TIMEOUT
- * if a wait hit its limit since the last call, else 0.  Synchronous. */
+/* Reads and clears the sticky error words of kernels with device-side waits
+ * (the TMA staging wait of vapr_backward, the pipeline waits of the
+ * tensor-core kernels): *code receives VAPR_ERR_TIMEOUT if a wait hit its
+ * limit since the last call, else 0.  Synchronous. */
 vapr_status vapr_device_error(int32_t* code);
 
 /* Copies the robot's device tables to the host and checks them: links in
@@ -190,6 +191,15 @@ vapr_status vapr_backward(const vapr_robot* robot, const float* q,
                           const float* dcost, int64_t n,
                           const vapr_format_table* table, void* jgrad_packed,
                           void* stream);
+
+/* ---- tensor-core GEMM (building block of the learned surrogate) ----------- */
+/* C = A * B^T on the tcgen05 tensor cores (TMA-fed shared memory, FP32
+ * accumulation in tensor memory).  A: bfloat16 [M][K], B: bfloat16 [N][K],
+ * both row-major with K contiguous; C: float32 [M][N] row-major.
+ * M % 128 == 0, N % 256 == 0, K % 64 == 0 and K > 0 (INVALID_ARG otherwise);
+ * A, B, C 16-byte aligned. */
+vapr_status vapr_gemm_bf16(const void* A, const void* B, float* C, int64_t M, int64_t N,
+                           int64_t K, void* stream);
 
 /* ---- the whole step ------------------------------------------------------ */
 /* Device workspace that vapr_cost_grad needs for n configurations: the

@@ -104,6 +104,7 @@ SIGNATURES = {
                                            ctypes.POINTER(vapr_format_table), _P, _P, _P, _P]),
     "vapr_backward": (ctypes.c_int, [ctypes.POINTER(vapr_robot), _P, _P, _P, _P, _i64,
                                      ctypes.POINTER(vapr_format_table), _P, _P]),
+    "vapr_gemm_bf16": (ctypes.c_int, [_P, _P, _P, _i64, _i64, _i64, _P]),
     "vapr_cost_grad_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(vapr_robot), _i64,
                                                          ctypes.POINTER(vapr_format_table)]),
     "vapr_cost_grad": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
@@ -361,3 +362,9 @@ def vapr_batched_publish(plan: "vapr_batch_plan", problem: int, stream=None):
 def vapr_batched_eval(plan: "vapr_batch_plan", dev_status, stream=None):
     _check(_load().vapr_batched_eval(ctypes.byref(plan), _ptr(dev_status), _stream(stream)),
            "vapr_batched_eval")
+
+
+def vapr_gemm_bf16(A, B_, C, M, N, K, stream=None):
+    """C[M,N] (float32) = A[M,K] @ B_[N,K]^T with bfloat16 A, B_ on tcgen05."""
+    _check(_load().vapr_gemm_bf16(_ptr(A), _ptr(B_), _ptr(C), M, N, K, _stream(stream)),
+           "vapr_gemm_bf16")

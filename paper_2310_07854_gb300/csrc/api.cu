@@ -267,8 +267,9 @@ size_t vapr_packed_row_bytes(int64_t row_len, vapr_format f) { return row_bytes(
 vapr_status vapr_device_error(int32_t* code) {
   if (!code) return VAPR_ERR_INVALID_ARG;
   const int v = backward_device_error(true);
-  if (v < 0) return cuda_status(cudaErrorUnknown);
-  *code = v;
+  const int w = tc_device_error(true);
+  if (v < 0 || w < 0) return cuda_status(cudaErrorUnknown);
+  *code = v ? v : w;
   return VAPR_OK;
 }
 

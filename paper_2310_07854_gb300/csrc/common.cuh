@@ -47,6 +47,8 @@ int sm_count();  // SMs of the current device (cached per device)
 int blocks_per_sm(const void* fn, int threads, size_t smem);
 
 int backward_device_error(bool reset);  // sticky device word of vapr_backward
+int tc_device_error(bool reset);        // sticky device word of the tensor-core kernels
+int* tc_error_word();                   // its device address (for kernel arguments)
 
 cudaError_t launch_fk(const RobotArgs& r, const float* q, int64_t n, Packed pos,
                       Packed xform, cudaStream_t st);

@@ -140,3 +140,12 @@ def test_batched_argument_checks():
     assert lib.vapr_batched_publish(byref(plan), 0, None) == 1
     assert lib.vapr_batched_plan(arr, 1, byref(ct), byref(B.vapr_batch_tuning(128, 0)),
                                  264, 1 << 20, byref(plan)) == 3    # plan buffer misaligned
+
+
+def test_gemm_argument_checks():
+    lib = B.lib()
+    assert lib.vapr_gemm_bf16(256, 256, 256, 100, 256, 64, None) == 1   # M % 128
+    assert lib.vapr_gemm_bf16(256, 256, 256, 128, 128, 64, None) == 1   # N % 256
+    assert lib.vapr_gemm_bf16(256, 256, 256, 128, 256, 32, None) == 1   # K % 64
+    assert lib.vapr_gemm_bf16(256, 256, 264, 128, 256, 64, None) == 3   # misaligned C
+    assert lib.vapr_gemm_bf16(256, 256, 256, 0, 256, 64, None) == 0     # empty
