@@ -428,3 +428,121 @@ void or_backward(int nj, const float* joint_fixed, int ns,
     free(T);
   }
 }
+
+/* ========================================================================= */
+/* Surrogate network: a plain forward pass and the chain rule, one sample at
+ * a time. */
+
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+static double silu_grad(double z) {
+  const double sg = 1.0 / (1.0 + exp(-z));
+  return sg * (1.0 + z * (1.0 - sg));
+}
+
+typedef struct {
+  const float *W1, *b1, *W2, *b2, *W3, *b3, *w4, *b4;
+} or_net;
+
+static or_net net_view(const float* p, int H) {
+  or_net v;
+  v.W1 = p;
+  v.b1 = v.W1 + 3 * H;
+  v.W2 = v.b1 + H;
+  v.b2 = v.W2 + H * H;
+  v.W3 = v.b2 + H;
+  v.b3 = v.W3 + H * H;
+  v.w4 = v.b3 + H;
+  v.b4 = v.w4 + H;
+  return v;
+}
+
+/* z1..z3 and a1..a3 of one sample (each length H); returns f */
+static double net_eval(const or_net* v, int H, const float* x, double* z1, double* a1, double* z2,
+                       double* a2, double* z3, double* a3) {
+  for (int i = 0; i < H; ++i) {
+    z1[i] = v->b1[i];
+    for (int k = 0; k < 3; ++k) z1[i] += (double)v->W1[3 * i + k] * x[k];
+    a1[i] = silu(z1[i]);
+  }
+  for (int i = 0; i < H; ++i) {
+    z2[i] = v->b2[i];
+    for (int k = 0; k < H; ++k) z2[i] += (double)v->W2[(int64_t)H * i + k] * a1[k];
+    a2[i] = silu(z2[i]);
+  }
+  for (int i = 0; i < H; ++i) {
+    z3[i] = v->b3[i];
+    for (int k = 0; k < H; ++k) z3[i] += (double)v->W3[(int64_t)H * i + k] * a2[k];
+    a3[i] = silu(z3[i]);
+  }
+  double f = v->b4[0];
+  for (int i = 0; i < H; ++i) f += (double)v->w4[i] * a3[i];
+  return f;
+}
+
+void or_mlp_forward(const float* params, int H, const float* x, int64_t n, double* out) {
+  or_net v = net_view(params, H);
+#pragma omp parallel
+  {
+    double* buf = (double*)malloc(sizeof(double) * 6 * (size_t)H);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+      out[i] = net_eval(&v, H, x + 3 * i, buf, buf + H, buf + 2 * H, buf + 3 * H, buf + 4 * H,
+                        buf + 5 * H);
+    free(buf);
+  }
+}
+
+double or_mlp_grads(const float* params, int H, const float* x, const float* y, int64_t n,
+                    double* grads) {
+  or_net v = net_view(params, H);
+  const int64_t P = 2 * (int64_t)H * H + 7 * (int64_t)H + 1;
+  for (int64_t i = 0; i < P; ++i) grads[i] = 0.0;
+  double* gW1 = grads;
+  double* gb1 = gW1 + 3 * H;
+  double* gW2 = gb1 + H;
+  double* gb2 = gW2 + (int64_t)H * H;
+  double* gW3 = gb2 + H;
+  double* gb3 = gW3 + (int64_t)H * H;
+  double* gw4 = gb3 + H;
+  double* gb4 = gw4 + H;
+  double* buf = (double*)malloc(sizeof(double) * 9 * (size_t)H);
+  double *z1 = buf, *a1 = buf + H, *z2 = buf + 2 * H, *a2 = buf + 3 * H, *z3 = buf + 4 * H,
+         *a3 = buf + 5 * H, *d3 = buf + 6 * H, *d2 = buf + 7 * H, *d1 = buf + 8 * H;
+  double loss = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    const float* xs = x + 3 * s;
+    const double f = net_eval(&v, H, xs, z1, a1, z2, a2, z3, a3);
+    const double r = f - (double)y[s];
+    loss += r * r / (double)n;
+    const double df = 2.0 * r / (double)n;  /* dL/df */
+    gb4[0] += df;
+    for (int i = 0; i < H; ++i) {
+      gw4[i] += df * a3[i];
+      d3[i] = df * v.w4[i] * silu_grad(z3[i]); /* dL/dz3 */
+    }
+    for (int i = 0; i < H; ++i) {
+      gb3[i] += d3[i];
+      for (int k = 0; k < H; ++k) gW3[(int64_t)H * i + k] += d3[i] * a2[k];
+    }
+    for (int k = 0; k < H; ++k) { /* dL/dz2 = (W3^T d3) * s'(z2) */
+      double acc = 0.0;
+      for (int i = 0; i < H; ++i) acc += (double)v.W3[(int64_t)H * i + k] * d3[i];
+      d2[k] = acc * silu_grad(z2[k]);
+    }
+    for (int i = 0; i < H; ++i) {
+      gb2[i] += d2[i];
+      for (int k = 0; k < H; ++k) gW2[(int64_t)H * i + k] += d2[i] * a1[k];
+    }
+    for (int k = 0; k < H; ++k) { /* dL/dz1 = (W2^T d2) * s'(z1) */
+      double acc = 0.0;
+      for (int i = 0; i < H; ++i) acc += (double)v.W2[(int64_t)H * i + k] * d2[i];
+      d1[k] = acc * silu_grad(z1[k]);
+    }
+    for (int i = 0; i < H; ++i) {
+      gb1[i] += d1[i];
+      for (int k = 0; k < 3; ++k) gW1[3 * i + k] += d1[i] * xs[k];
+    }
+  }
+  free(buf);
+  return loss;
+}

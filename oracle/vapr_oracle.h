@@ -102,6 +102,15 @@ void or_backward(int nj, const float* joint_fixed, int ns,
 void or_scene_sdf(int no, const float* pose, const float* half,
                   const double* pts, int64_t m, double* out);
 
+/* ---- signed-distance surrogate network (project addition) ---------------- */
+/* f(x) = w4 . s(W3 s(W2 s(W1 x + b1) + b2) + b3) + b4 with s(z) = z/(1+e^-z)
+ * (SiLU) and hidden width H.  params (float32) in the order W1[H][3], b1[H],
+ * W2[H][H], b2[H], W3[H][H], b3[H], w4[H], b4[1] (2H^2 + 7H + 1 values). */
+void or_mlp_forward(const float* params, int H, const float* x, int64_t n, double* out);
+/* L = mean_i (f(x_i) - y_i)^2 and dL/dparams (same order, double). */
+double or_mlp_grads(const float* params, int H, const float* x, const float* y, int64_t n,
+                    double* grads);
+
 int or_num_threads(void);
 
 #ifdef __cplusplus
