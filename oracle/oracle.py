@@ -72,7 +72,8 @@ def _load():
             "or_backward": (None, [i32, P, i32, P, P, P, P, P, i64, P]),
             "or_scene_sdf": (None, [i32, P, P, P, i64, P]),
             "or_mlp_forward": (None, [P, i32, P, i64, P]),
-            "or_mlp_grads": (dbl, [P, i32, P, P, i64, P]),
+            "or_mlp_forward_bf16act": (None, [P, i32, P, i64, P]),
+            "or_mlp_grads": (dbl, [P, i32, P, P, i64, dbl, P]),
             "or_num_threads": (i32, []),
         }
         for name, (res, args) in sig.items():
@@ -254,20 +255,23 @@ def mlp_param_count(H: int = 256) -> int:
     return 2 * H * H + 7 * H + 1
 
 
-def mlp_forward(params, x, H: int = 256):
-    """f(x) for points x [n, 3] (float32 params in the documented order)."""
+def mlp_forward(params, x, H: int = 256, bf16_activations: bool = False):
+    """f(x) for points x [n, 3] (float32 params in the documented order).
+    bf16_activations rounds the inputs of the two H x H layers to bfloat16."""
     params = _c(params, np.float32)
     x = _c(x, np.float32).reshape(-1, 3)
     out = np.empty(x.shape[0], np.float64)
-    _load().or_mlp_forward(_p(params), H, _p(x), x.shape[0], _p(out))
+    fn = _load().or_mlp_forward_bf16act if bf16_activations else _load().or_mlp_forward
+    fn(_p(params), H, _p(x), x.shape[0], _p(out))
     return out
 
 
-def mlp_grads(params, x, y, H: int = 256):
-    """(loss, dloss/dparams) of the mean squared error."""
+def mlp_grads(params, x, y, H: int = 256, over_weight: float = 1.0):
+    """(loss, dloss/dparams) of the squared error, residuals f > y weighted
+    by over_weight (1: the mean squared error)."""
     params = _c(params, np.float32)
     x = _c(x, np.float32).reshape(-1, 3)
     y = _c(y, np.float32)
     g = np.empty(mlp_param_count(H), np.float64)
-    loss = _load().or_mlp_grads(_p(params), H, _p(x), _p(y), x.shape[0], _p(g))
+    loss = _load().or_mlp_grads(_p(params), H, _p(x), _p(y), x.shape[0], float(over_weight), _p(g))
     return float(loss), g

@@ -479,6 +479,41 @@ static double net_eval(const or_net* v, int H, const float* x, double* z1, doubl
   return f;
 }
 
+static double round_bf16(double v) {
+  return or_exmy_decode(or_exmy_encode((float)v, 8, 7, OR_IEEE), 8, 7, OR_IEEE);
+}
+
+void or_mlp_forward_bf16act(const float* params, int H, const float* x, int64_t n, double* out) {
+  or_net v = net_view(params, H);
+#pragma omp parallel
+  {
+    double* a1 = (double*)malloc(sizeof(double) * 2 * (size_t)H);
+    double* a2 = a1 + H;
+#pragma omp for schedule(static)
+    for (int64_t s = 0; s < n; ++s) {
+      const float* xs = x + 3 * s;
+      for (int i = 0; i < H; ++i) {
+        double z = v.b1[i];
+        for (int k = 0; k < 3; ++k) z += (double)v.W1[3 * i + k] * xs[k];
+        a1[i] = round_bf16(silu(z));
+      }
+      for (int i = 0; i < H; ++i) {
+        double z = v.b2[i];
+        for (int k = 0; k < H; ++k) z += (double)v.W2[(int64_t)H * i + k] * a1[k];
+        a2[i] = round_bf16(silu(z));
+      }
+      double f = v.b4[0];
+      for (int i = 0; i < H; ++i) {
+        double z = v.b3[i];
+        for (int k = 0; k < H; ++k) z += (double)v.W3[(int64_t)H * i + k] * a2[k];
+        f += (double)v.w4[i] * silu(z);
+      }
+      out[s] = f;
+    }
+    free(a1);
+  }
+}
+
 void or_mlp_forward(const float* params, int H, const float* x, int64_t n, double* out) {
   or_net v = net_view(params, H);
 #pragma omp parallel
@@ -493,7 +528,7 @@ void or_mlp_forward(const float* params, int H, const float* x, int64_t n, doubl
 }
 
 double or_mlp_grads(const float* params, int H, const float* x, const float* y, int64_t n,
-                    double* grads) {
+                    double over_weight, double* grads) {
   or_net v = net_view(params, H);
   const int64_t P = 2 * (int64_t)H * H + 7 * (int64_t)H + 1;
   for (int64_t i = 0; i < P; ++i) grads[i] = 0.0;
@@ -513,8 +548,9 @@ double or_mlp_grads(const float* params, int H, const float* x, const float* y, 
     const float* xs = x + 3 * s;
     const double f = net_eval(&v, H, xs, z1, a1, z2, a2, z3, a3);
     const double r = f - (double)y[s];
-    loss += r * r / (double)n;
-    const double df = 2.0 * r / (double)n;  /* dL/df */
+    const double wt = r > 0.0 ? over_weight : 1.0;
+    loss += wt * r * r / (double)n;
+    const double df = 2.0 * wt * r / (double)n;  /* dL/df */
     gb4[0] += df;
     for (int i = 0; i < H; ++i) {
       gw4[i] += df * a3[i];

@@ -107,9 +107,16 @@ void or_scene_sdf(int no, const float* pose, const float* half,
  * (SiLU) and hidden width H.  params (float32) in the order W1[H][3], b1[H],
  * W2[H][H], b2[H], W3[H][H], b3[H], w4[H], b4[1] (2H^2 + 7H + 1 values). */
 void or_mlp_forward(const float* params, int H, const float* x, int64_t n, double* out);
-/* L = mean_i (f(x_i) - y_i)^2 and dL/dparams (same order, double). */
+/* The same network with the inputs of the two H x H layers (the activations
+ * s(z1) and s(z2)) rounded to float32 and then to bfloat16 (E8M7, round to
+ * nearest even) before use: the rounding points of a bfloat16 tensor-core
+ * evaluation.  Weights are used as given (pass them already rounded). */
+void or_mlp_forward_bf16act(const float* params, int H, const float* x, int64_t n, double* out);
+/* L = mean_i w_i (f(x_i) - y_i)^2 with w_i = over_weight where f(x_i) > y_i
+ * and 1 elsewhere (over_weight = 1: the mean squared error), and dL/dparams
+ * (same order, double); w is piecewise constant, so dL/df_i = 2 w_i r_i / n. */
 double or_mlp_grads(const float* params, int H, const float* x, const float* y, int64_t n,
-                    double* grads);
+                    double over_weight, double* grads);
 
 int or_num_threads(void);
 

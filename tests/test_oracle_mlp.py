@@ -56,15 +56,18 @@ def test_silu_identities_through_the_net(orc):
         assert s(-z) == pytest.approx(s(z) - z, abs=1e-14)
 
 
-@pytest.mark.parametrize("H", [3, 8])
-def test_gradients_match_finite_differences(orc, H):
+@pytest.mark.parametrize("H,ow", [(3, 1.0), (8, 1.0), (8, 4.0)])
+def test_gradients_match_finite_differences(orc, H, ow):
     rng = np.random.default_rng(H)
     p = _params(H, H)
     x = rng.uniform(-0.8, 0.8, (6, 3)).astype(np.float32)
-    y = rng.uniform(-0.3, 0.3, 6).astype(np.float32)
-    loss, g = orc.mlp_grads(p, x, y, H)
-    assert loss == pytest.approx(np.mean((orc.mlp_forward(p, x, H) - y) ** 2), rel=1e-12)
-    h = 2.0 ** -12  # parameters are float32: step exactly representable
+    # targets on both sides of the network's output
+    y = (orc.mlp_forward(p, x, H) + np.array([0.3, -0.2, 0.25, -0.3, 0.1, -0.15])).astype(np.float32)
+    loss, g = orc.mlp_grads(p, x, y, H, over_weight=ow)
+    r = orc.mlp_forward(p, x, H) - y
+    assert (r > 0).any() and (r < 0).any()
+    assert loss == pytest.approx(np.mean(np.where(r > 0, ow, 1.0) * r ** 2), rel=1e-12)
+    h = 2.0 ** -14  # parameters are float32: the step actually taken is used below
     for name, sl in _slices(H).items():
         idx = np.arange(sl.start, sl.stop)
         for i in rng.choice(idx, min(6, idx.size), replace=False):
@@ -72,5 +75,35 @@ def test_gradients_match_finite_differences(orc, H):
             pp[i] += np.float32(h)
             pm[i] -= np.float32(h)
             dh = float(pp[i]) - float(pm[i])
-            fd = (orc.mlp_grads(pp, x, y, H)[0] - orc.mlp_grads(pm, x, y, H)[0]) / dh
+            fd = (orc.mlp_grads(pp, x, y, H, over_weight=ow)[0]
+                  - orc.mlp_grads(pm, x, y, H, over_weight=ow)[0]) / dh
             assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9), (name, i)
+
+
+def test_bf16_activation_rounding_points(orc):
+    """One unit per layer: the bfloat16 variant rounds s(z1) and s(z2) (via
+    float32, ties to even, as torch's bfloat16 cast does) and nothing else."""
+    import torch
+    H = 1
+    sl = _slices(H)
+    p = np.zeros(10, np.float32)
+    p[sl["W1"]] = [1.0, 0.0, 0.0]
+    p[sl["W2"]] = 1.0
+    p[sl["W3"]] = 1.0
+    p[sl["w4"]] = 1.0
+    s = lambda z: z / (1 + math.exp(-z))
+    bf = lambda v: float(torch.tensor(v, dtype=torch.float32).to(torch.bfloat16).double())
+    for z in (-3.0, -0.5, 0.0, 0.75, 4.0, 1.3125):
+        x = np.array([[z, 0.0, 0.0]], np.float32)
+        want = s(bf(s(bf(s(z)))))
+        assert orc.mlp_forward(p, x, H, bf16_activations=True)[0] == pytest.approx(want, abs=1e-15)
+
+
+def test_bf16_variant_equals_plain_when_hidden_layers_are_off(orc):
+    """W3 = 0: the output depends on b3 only, so rounding a1 and a2 changes nothing."""
+    H = 8
+    p = _params(H, 3)
+    sl = _slices(H)
+    p[sl["W3"]] = 0.0
+    x = np.random.default_rng(1).uniform(-1, 1, (16, 3)).astype(np.float32)
+    assert np.array_equal(orc.mlp_forward(p, x, H), orc.mlp_forward(p, x, H, bf16_activations=True))
