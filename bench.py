@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -48,6 +50,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dram-scale", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the learned-surrogate leg (training + gated collision)")
+    ap.add_argument("--surrogate-epochs", type=int, default=80)
     ap.add_argument("--configs", type=int, default=0,
                     help="override the batch size (configurations per GPU)")
     return ap.parse_args()
@@ -208,6 +213,99 @@ def kernel_traffic(stage: str, table: str):
     return ent.get("dram_bytes_per_config")
 
 
+def time_graph(fn, steps, warmup, flush_buf, torch):
+    """Mean device ms of fn() captured in a CUDA graph, L2 flushed before
+    each replay (outside the events)."""
+    st = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ts = []
+    for i in range(warmup + steps):
+        flush_buf.add_(1)
+        e0.record(st)
+        g.replay()
+        e1.record(st)
+        st.synchronize()
+        if i >= warmup:
+            ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts)
+
+
+def surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind):
+    """Learned signed-distance surrogate of the workload's scene: trained on
+    2M exact distances, then used as the broad phase of the collision stage
+    on the workload's sphere centres.  Reports training time and loss, the
+    network's distance error against the exact kernel, the share of spheres
+    it clears, missed contacts (must be 0), and the gated collision stage's
+    speed against the plain FP32 collision stage."""
+    from paper_2310_07854_gb300 import binding as B
+    from paper_2310_07854_gb300 import surrogate as SG
+    S = w.robot.n_spheres
+    sg = SG.Surrogate(ev32.scene, synth.init_mlp_params(5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u, y = sg.training_set(seed=5)
+    losses = sg.train(u, y, epochs=args.surrogate_epochs)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del u, y
+    delta = sg.calibrate(seed=99, eta=w.params.eta)
+    ev32.fk(q, n)
+    ev32.collision(n)
+    exact = (ev32.cost[:n].clone(), ev32.dist[:n].clone(), ev32.grad[:n].clone())
+    cost = torch.empty(n, device="cuda")
+    dist = torch.empty_like(ev32.dist[:n])
+    grad = torch.empty_like(ev32.grad[:n])
+    est = torch.empty((n, S), device="cuda")
+    gated = lambda: sg.collision_cost(ev32.robot, ev32.params, ev32.pos, n, F.FP32_TABLE, cost,
+                                      dist, grad, est)
+    gated()
+    torch.cuda.synchronize()
+    c = ev32.pos[:n].view(torch.float32)[:, :3 * S].reshape(-1, 3).contiguous()
+    r = torch.as_tensor(np.tile(w.robot.sphere_local[:, 3], n), device="cuda")
+    sdf = torch.empty(n * S, device="cuda")
+    B.vapr_scene_sdf(ev32.scene, c, n * S, sdf)
+    e = est.reshape(-1)
+    skipped = (e - r) >= sg.domain.margin
+    miss = int((skipped & (sdf < r + w.params.eta)).sum())
+    uq, _ = sg.samples(c)
+    inside = (uq.abs() <= 1).all(1)
+    band = inside & (sdf >= SG.Y_MIN) & (sdf <= SG.Y_MAX)
+    err = (e - sdf).abs()
+    t_exact = time_graph(lambda: ev32.collision(n), args.steps, args.warmup, flush, torch)
+    t_gated = time_graph(gated, args.steps, args.warmup, flush, torch)
+    f = torch.empty(n * S, device="cuda")
+    t_net = time_graph(lambda: sg.forward_into(uq, f), args.steps, args.warmup, flush, torch)
+    t_sdf = time_graph(lambda: B.vapr_scene_sdf(ev32.scene, c, n * S, sdf), args.steps, args.warmup,
+                       flush, torch)
+    nq = n * S
+    tc_flops = 2.0 * 2 * 256 * 256 * nq  # the two tensor-core layers
+    tflops = tc_flops / (t_net / 1000.0) / 1e12
+    return {
+        "queries": nq, "cuboids": w.scene.n_cuboids, "train_points": 2_000_000,
+        "train_epochs": args.surrogate_epochs, "train_s": train_s, "loss_first_last": [losses[0], losses[-1]],
+        "cleared": float(skipped.float().mean()),
+        "clearable": float(((sdf - r) >= sg.domain.margin).float().mean()),
+        "missed_contacts": miss,
+        "equal_to_exact": all(torch.equal(a, b) for a, b in zip(exact, (cost, dist, grad))),
+        "max_dist_err_band_m": float(err[band].max()), "rms_dist_err_band_m": float(err[band].square().mean().sqrt()),
+        "band_m": [SG.Y_MIN, SG.Y_MAX], "margin_m": sg.domain.margin,
+        "validation_max_overestimate_m": delta,
+        "ms": {"exact_collision": t_exact, "gated_collision": t_gated, "network_only": t_net,
+               "exact_sdf_min_over_cuboids": t_sdf},
+        "speedup_vs_fp32_collision": t_exact / t_gated,
+        "network_roofline": {"bound": "tensor", "achieved": tflops, "unit": "TFLOP/s",
+                             "peak": peaks.get("bf16_tflops"), "frac": tflops / peaks["bf16_tflops"]
+                             if peaks.get("bf16_tflops") else None, "peak_source": peak_kind,
+                             "flops_per_query": 2 * 2 * 256 * 256},
+    }
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -326,6 +424,10 @@ def main():
                 dram[name][k] = {"ms": ms, "hbm_frac": bp[k] * nb / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]}
         del ebig, ebv, qb
 
+    sur = None
+    if not args.no_surrogate:
+        sur = surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind)
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(args.workload, args.cpu_seconds)
@@ -351,6 +453,7 @@ def main():
             "clocks": clocks,
             "cpu_baseline": cb,
             "dram_scale": dram,
+            "surrogate": sur,
         }
         print(json.dumps(line), flush=True)
     if pg:

@@ -308,6 +308,110 @@ vapr_status vapr_cost_grad_noalloc(const vapr_robot* robot, const vapr_scene* sc
                                    float* cost, void* dist_packed, void* jgrad_packed,
                                    void* stream);
 
+/* ---- learned signed-distance surrogate ------------------------------------ */
+/* A per-scene network estimating the scene signed distance
+ * sdf(p) = min_o d_o(p) (the box distance of vapr_collision_cost), used as a
+ * broad phase in front of the exact collision test.  The paper has no
+ * counterpart; the library adds it.  The network, of domain coordinates u:
+ *   f(u) = w4 . s(W3 s(W2 s(W1 u + b1) + b2) + b3) + b4,  s(z) = z/(1+e^-z)
+ * with hidden width 256.  The two 256 x 256 layers run on the tcgen05 tensor
+ * cores: bfloat16 weights and activations, float32 accumulation; layer 1,
+ * the biases, the output dot product and the master weights are float32.
+ * Parameters (float32) in this order, W rows being output units:
+ *   W1[256][3], b1[256], W2[256][256], b2[256], W3[256][256], b3[256],
+ *   w4[256], b4  (VAPR_MLP_PARAMS values). */
+#define VAPR_MLP_HIDDEN 256
+#define VAPR_MLP_PARAMS (2 * 256 * 256 + 7 * 256 + 1)
+
+/* Bytes of a network state (device memory the caller allocates, 256-byte
+ * aligned): master parameters, Adam moments and step, bfloat16 W2, W3 and
+ * their transposes. */
+size_t vapr_mlp_state_bytes(void);
+
+/* Loads parameters (device float32 [VAPR_MLP_PARAMS]) into `state`, zeroes
+ * the Adam moments and step and builds the bfloat16 copies. */
+vapr_status vapr_mlp_init(void* state, const float* params, void* stream);
+
+/* Copies the master parameters out (device float32 [VAPR_MLP_PARAMS]). */
+vapr_status vapr_mlp_get_params(const void* state, float* params, void* stream);
+
+/* out[i] = f(u_i) for u float32 [n][3], out float32 [n].
+ * One persistent launch: 128 inputs per tile, layer 1 on the CUDA cores,
+ * layers 2 and 3 on the tensor cores with the weights streamed through
+ * shared memory by TMA, the activations kept on chip. */
+vapr_status vapr_mlp_forward(const void* state, const float* u, int64_t n, float* out,
+                             void* stream);
+
+/* Training workspace for batches of `batch` samples: 0 unless batch is a
+ * positive multiple of 128 and at most 1 << 20. */
+size_t vapr_mlp_workspace_bytes(int64_t batch);
+
+/* Squared-error loss L = mean_i w_i (f(u_i) - y_i)^2 over one batch, with
+ * w_i = over_weight where f(u_i) > y_i and 1 elsewhere (over_weight = 1: the
+ * mean squared error; > 1 penalises overestimates, making the network a
+ * more conservative distance estimate), and dL/dparams (same order as the
+ * parameters) by the backward pass: forward GEMMs with fused bias, SiLU and
+ * head epilogues, backward GEMMs for dL/dA and, split over the batch, for
+ * dL/dW.  u float32 [batch][3], y float32 [batch]; over_weight > 0;
+ * workspace: device, 256-byte aligned, vapr_mlp_workspace_bytes(batch)
+ * bytes (INVALID_ARG if smaller); grads: NULL or float32 [VAPR_MLP_PARAMS];
+ * loss: NULL or float32 [1].  Deterministic: no atomics in the sums. */
+vapr_status vapr_mlp_grads(const void* state, const float* u, const float* y, int64_t batch,
+                           float over_weight, void* workspace, size_t workspace_bytes,
+                           float* grads, float* loss, void* stream);
+
+/* Training hyper-parameters: Adam (Kingma and Ba) step size, moment decay
+ * rates and epsilon, and the loss weight of overestimates. */
+typedef struct {
+  float lr, beta1, beta2, eps;
+  float over_weight;
+} vapr_train_params;
+
+/* vapr_mlp_grads, then one Adam step on the master parameters (bias-corrected
+ * with the state's step count, which it increments) and a refresh of the
+ * bfloat16 copies.  All stream work; capturable in a CUDA graph. */
+vapr_status vapr_mlp_train_step(void* state, const float* u, const float* y, int64_t batch,
+                                const vapr_train_params* hp, void* workspace,
+                                size_t workspace_bytes, float* loss, void* stream);
+
+/* Exact scene signed distance sdf(p) = min_o d_o(p) of points p
+ * (float32 [n][3]) -> sdf float32 [n]; +FLT_MAX with no cuboids. */
+vapr_status vapr_scene_sdf(const vapr_scene* scene, const float* pts, int64_t n, float* sdf,
+                           void* stream);
+
+/* Where the network applies and how it gates the exact test. */
+typedef struct {
+  float lo[3], hi[3]; /* domain box: u = 2 (p - lo) / (hi - lo) - 1 */
+  float pad;          /* every cuboid lies inside the box shrunk by pad metres */
+  float margin;       /* a sphere takes the exact test when estimate - r < margin */
+} vapr_surrogate_domain;
+
+/* Training samples: u = domain coordinates of p, y = sdf(p) (exact) clamped
+ * to [y_min, y_max] (a truncated distance: only the band near the surfaces
+ * decides the gate; pass -FLT_MAX, FLT_MAX for the plain distance).
+ * pts float32 [n][3] -> u float32 [n][3], y float32 [n]. */
+vapr_status vapr_surrogate_samples(const vapr_scene* scene, const vapr_surrogate_domain* domain,
+                                   const float* pts, int64_t n, float y_min, float y_max,
+                                   float* u, float* y, void* stream);
+
+/* The collision stage with the network as a broad phase.  For each sphere
+ * centre c of each configuration the estimate is f(u(c)) inside the domain
+ * box and, outside it, dist(c, box) + pad, a lower bound of sdf(c).  A
+ * sphere whose estimate - r >= margin skips the sphere-cuboid tests; the
+ * others, and all self-collision pairs, run the exact test of
+ * vapr_collision_cost.  Results (cost, D, G) equal vapr_collision_cost
+ * whenever every skipped sphere is truly clear (sdf(c) >= r + eta), which
+ * holds when the network's error on the skipped spheres stays below
+ * margin - eta.  estimate: float32 [n][S], written (the estimates, for
+ * checking against vapr_scene_sdf).  Other arguments as vapr_collision_cost. */
+vapr_status vapr_surrogate_collision_cost(const vapr_robot* robot, const vapr_scene* scene,
+                                          const vapr_cost_params* params, const void* mlp_state,
+                                          const vapr_surrogate_domain* domain,
+                                          const void* pos_packed, int64_t n,
+                                          const vapr_format_table* table, float* cost,
+                                          void* dist_packed, void* grad_packed, float* estimate,
+                                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,16 @@ class vapr_batch_tuning(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
 
 
+class vapr_train_params(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("over_weight", ctypes.c_float)]
+
+
+class vapr_surrogate_domain(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("pad", ctypes.c_float),
+                ("margin", ctypes.c_float)]
+
+
 class vapr_batch_plan(ctypes.Structure):
     _fields_ = [("opaque", ctypes.c_uint64 * 160)]
 
@@ -124,6 +134,25 @@ SIGNATURES = {
                                               ctypes.POINTER(vapr_cost_params), _P, _i64,
                                               ctypes.POINTER(vapr_format_table), _P, _P, _P, _P,
                                               _P]),
+    "vapr_mlp_state_bytes": (ctypes.c_size_t, []),
+    "vapr_mlp_init": (ctypes.c_int, [_P, _P, _P]),
+    "vapr_mlp_get_params": (ctypes.c_int, [_P, _P, _P]),
+    "vapr_mlp_forward": (ctypes.c_int, [_P, _P, _i64, _P, _P]),
+    "vapr_mlp_workspace_bytes": (ctypes.c_size_t, [_i64]),
+    "vapr_mlp_grads": (ctypes.c_int, [_P, _P, _P, _i64, ctypes.c_float, _P, ctypes.c_size_t, _P,
+                                      _P, _P]),
+    "vapr_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _i64, ctypes.POINTER(vapr_train_params),
+                                           _P, ctypes.c_size_t, _P, _P]),
+    "vapr_scene_sdf": (ctypes.c_int, [ctypes.POINTER(vapr_scene), _P, _i64, _P, _P]),
+    "vapr_surrogate_samples": (ctypes.c_int, [ctypes.POINTER(vapr_scene),
+                                              ctypes.POINTER(vapr_surrogate_domain), _P, _i64,
+                                              ctypes.c_float, ctypes.c_float, _P, _P, _P]),
+    "vapr_surrogate_collision_cost": (ctypes.c_int, [ctypes.POINTER(vapr_robot),
+                                                     ctypes.POINTER(vapr_scene),
+                                                     ctypes.POINTER(vapr_cost_params), _P,
+                                                     ctypes.POINTER(vapr_surrogate_domain), _P,
+                                                     _i64, ctypes.POINTER(vapr_format_table), _P,
+                                                     _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -368,3 +397,101 @@ def vapr_gemm_bf16(A, B_, C, M, N, K, stream=None):
     """C[M,N] (float32) = A[M,K] @ B_[N,K]^T with bfloat16 A, B_ on tcgen05."""
     _check(_load().vapr_gemm_bf16(_ptr(A), _ptr(B_), _ptr(C), M, N, K, _stream(stream)),
            "vapr_gemm_bf16")
+
+
+# ---------------------------------------------------------------- surrogate
+MLP_HIDDEN = 256
+MLP_PARAMS = 2 * 256 * 256 + 7 * 256 + 1
+
+
+def vapr_mlp_state_bytes() -> int:
+    return int(_load().vapr_mlp_state_bytes())
+
+
+def alloc_mlp_state(device="cuda"):
+    """A uint8 tensor of vapr_mlp_state_bytes() bytes (256-byte aligned)."""
+    import torch
+    return torch.empty(vapr_mlp_state_bytes(), dtype=torch.uint8, device=device)
+
+
+def vapr_mlp_init(state, params, stream=None):
+    _check(_load().vapr_mlp_init(_ptr(state), _ptr(params), _stream(stream)), "vapr_mlp_init")
+
+
+def vapr_mlp_get_params(state, params, stream=None):
+    _check(_load().vapr_mlp_get_params(_ptr(state), _ptr(params), _stream(stream)),
+           "vapr_mlp_get_params")
+
+
+def vapr_mlp_forward(state, u, n, out, stream=None):
+    _check(_load().vapr_mlp_forward(_ptr(state), _ptr(u), n, _ptr(out), _stream(stream)),
+           "vapr_mlp_forward")
+
+
+def vapr_mlp_workspace_bytes(batch: int) -> int:
+    return int(_load().vapr_mlp_workspace_bytes(batch))
+
+
+def alloc_mlp_workspace(batch: int, device="cuda"):
+    import torch
+    nb = vapr_mlp_workspace_bytes(batch)
+    if nb == 0:
+        raise VaprError(1, "vapr_mlp_workspace_bytes")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def vapr_mlp_grads(state, u, y, batch, workspace, grads=None, loss=None, over_weight=1.0,
+                   stream=None):
+    _check(_load().vapr_mlp_grads(_ptr(state), _ptr(u), _ptr(y), batch, over_weight, _ptr(workspace),
+                                  workspace.numel() if workspace is not None else 0, _ptr(grads),
+                                  _ptr(loss), _stream(stream)), "vapr_mlp_grads")
+
+
+def vapr_mlp_train_step(state, u, y, batch, hp, workspace, loss=None, stream=None):
+    """hp: vapr_train_params or (lr, beta1, beta2, eps[, over_weight])."""
+    if isinstance(hp, vapr_train_params):
+        a = hp
+    else:
+        hp = tuple(hp)
+        a = vapr_train_params(*(hp + (1.0,) * (5 - len(hp))))
+    _check(_load().vapr_mlp_train_step(_ptr(state), _ptr(u), _ptr(y), batch, ctypes.byref(a),
+                                       _ptr(workspace),
+                                       workspace.numel() if workspace is not None else 0,
+                                       _ptr(loss), _stream(stream)), "vapr_mlp_train_step")
+
+
+def vapr_scene_sdf(scene: DeviceScene, pts, n, sdf, stream=None):
+    _check(_load().vapr_scene_sdf(ctypes.byref(scene.c), _ptr(pts), n, _ptr(sdf), _stream(stream)),
+           "vapr_scene_sdf")
+
+
+def surrogate_domain(lo, hi, pad, margin) -> vapr_surrogate_domain:
+    d = vapr_surrogate_domain()
+    for j in range(3):
+        d.lo[j] = float(lo[j])
+        d.hi[j] = float(hi[j])
+    d.pad = float(pad)
+    d.margin = float(margin)
+    return d
+
+
+FLT_MAX = float(np.finfo(np.float32).max)
+
+
+def vapr_surrogate_samples(scene: DeviceScene, domain: vapr_surrogate_domain, pts, n, u, y,
+                           y_min=-FLT_MAX, y_max=FLT_MAX, stream=None):
+    _check(_load().vapr_surrogate_samples(ctypes.byref(scene.c), ctypes.byref(domain), _ptr(pts), n,
+                                          y_min, y_max, _ptr(u), _ptr(y), _stream(stream)),
+           "vapr_surrogate_samples")
+
+
+def vapr_surrogate_collision_cost(robot: DeviceRobot, scene: DeviceScene, params, state,
+                                  domain: vapr_surrogate_domain, pos_packed, n, table, cost=None,
+                                  dist_packed=None, grad_packed=None, estimate=None, stream=None):
+    ct = to_c_table(table)
+    cp = params if isinstance(params, vapr_cost_params) else cost_params(params)
+    _check(_load().vapr_surrogate_collision_cost(
+        ctypes.byref(robot.c), ctypes.byref(scene.c), ctypes.byref(cp), _ptr(state),
+        ctypes.byref(domain), _ptr(pos_packed), n, ctypes.byref(ct), _ptr(cost),
+        _ptr(dist_packed), _ptr(grad_packed), _ptr(estimate), _stream(stream)),
+        "vapr_surrogate_collision_cost")

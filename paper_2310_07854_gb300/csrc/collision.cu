@@ -39,6 +39,8 @@ struct CollArgs {
   Packed pos, dist, grad;
   float* cost;
   int64_t n;
+  const float* est;  // MASKED: per-sphere distance estimates [n][S]
+  float margin;
 };
 
 // Carves the block's tables and every warp's working set; keeps warp `mine`'s.
@@ -53,6 +55,7 @@ __host__ __device__ inline void carve_coll(Bump& b, const RobotArgs& r, int O, R
   }
 }
 
+template <bool MASKED>
 __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs a) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -74,15 +77,16 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
     out.cost = a.cost ? a.cost + c : nullptr;
     out.dist = a.dist.ptr ? reinterpret_cast<uint32_t*>(a.dist.ptr + c * a.dist.stride) : nullptr;
     out.grad = a.grad.ptr ? reinterpret_cast<uint32_t*>(a.grad.ptr + c * a.grad.stride) : nullptr;
-    collision_config(a.r, a.sc.O, rb, sm, w,
-                     reinterpret_cast<const uint32_t*>(a.pos.ptr + c * a.pos.stride), a.pos.f,
-                     a.dist.f, a.grad.f, a.eta, a.w_c, a.w_s, out, lane);
+    collision_config<false, MASKED>(a.r, a.sc.O, rb, sm, w,
+                                    reinterpret_cast<const uint32_t*>(a.pos.ptr + c * a.pos.stride),
+                                    a.pos.f, a.dist.f, a.grad.f, a.eta, a.w_c, a.w_s, out, lane,
+                                    MASKED ? a.est + c * a.r.S : nullptr, a.margin);
   }
 }
 
 cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc, const vapr_cost_params& p,
                              Packed pos, int64_t n, float* cost, Packed dist, Packed grad,
-                             cudaStream_t st) {
+                             cudaStream_t st, const float* est, float margin) {
   CollArgs a;
   a.r = r;
   a.sc = sc;
@@ -95,17 +99,23 @@ cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc, const vapr
   a.grad = grad;
   a.cost = cost;
   a.n = n;
+  a.est = est;
+  a.margin = margin;
   Bump b(nullptr);
   RobotSm rb;
   SceneSm sm;
   CollWarp w;
   carve_coll(b, r, sc.O, rb, sm, w, 0);
   const size_t smem = b.bytes();
-  const int per_sm = blocks_per_sm((const void*)collision_kernel, COLL_WARPS * 32, smem);
+  const void* fn = est ? (const void*)collision_kernel<true> : (const void*)collision_kernel<false>;
+  const int per_sm = blocks_per_sm(fn, COLL_WARPS * 32, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   const int64_t blocks = (n + COLL_WARPS - 1) / COLL_WARPS;
-  const int64_t cap = (int64_t)sm_count() * per_sm;
-  collision_kernel<<<(int)(blocks < cap ? blocks : cap), COLL_WARPS * 32, smem, st>>>(a);
+  const int grid = (int)(blocks < (int64_t)sm_count() * per_sm ? blocks : (int64_t)sm_count() * per_sm);
+  if (est)
+    collision_kernel<true><<<grid, COLL_WARPS * 32, smem, st>>>(a);
+  else
+    collision_kernel<false><<<grid, COLL_WARPS * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

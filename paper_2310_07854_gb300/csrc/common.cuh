@@ -54,7 +54,8 @@ cudaError_t launch_fk(const RobotArgs& r, const float* q, int64_t n, Packed pos,
                       Packed xform, cudaStream_t st);
 cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc,
                              const vapr_cost_params& p, Packed pos, int64_t n,
-                             float* cost, Packed dist, Packed grad, cudaStream_t st);
+                             float* cost, Packed dist, Packed grad, cudaStream_t st,
+                             const float* est = nullptr, float margin = 0.f);
 cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform,
                             Packed grad, const float* dcost, int64_t n,
                             Packed jgrad, cudaStream_t st);

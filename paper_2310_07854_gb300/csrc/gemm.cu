@@ -60,20 +60,6 @@ bool tg_tensor_map(CUtensorMap* map, const void* ptr, uint64_t K, uint64_t rows,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Epilogue: FP32 rows of C (split z writes its own C slab).
-struct StoreF32 {
-  float* C;
-  int N;
-  int64_t slab;  // elements per split
-  __device__ __forceinline__ void operator()(int row, int col0, const uint32_t (&r)[32], int z) const {
-    float4* out = reinterpret_cast<float4*>(C + z * slab + (int64_t)row * N + col0);
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      out[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                           __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-  }
-};
-
 }  // namespace vapr
 
 using namespace vapr;

@@ -182,6 +182,7 @@ struct CollWarp {
   uint32_t* queue;  // [QCAP] sphere | cuboid << 16
   int* ccount;      // [J]
   uint16_t* cand;   // [J][CHUNK] candidate cuboids of each link
+  uint32_t* far;    // [MAX_SPHERES / 32] spheres cleared by a broad-phase estimate
 };
 
 __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp& w) {
@@ -191,6 +192,7 @@ __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp&
   w.queue = b.take<uint32_t>(QCAP);
   w.ccount = b.take<int>(J);
   w.cand = b.take<uint16_t>((size_t)J * CHUNK);
+  w.far = b.take<uint32_t>(VAPR_MAX_SPHERES / 32);
 }
 
 // Radii into P[].w and zero accumulators (once per robot).
@@ -271,14 +273,17 @@ struct CollOut {
 // cost, D and G rows out.  Culling is conservative (see collision.cu).
 // COHERENT reads the P row with loads that see writes made earlier in the
 // same kernel (the fused multi-problem kernel); otherwise through the
-// read-only cache.
-template <bool COHERENT = false>
+// read-only cache.  MASKED takes a per-sphere distance estimate `est` (this
+// configuration's row): spheres with est - r >= margin skip the cuboid
+// tests, and only the others shape the link bounding spheres.
+template <bool COHERENT = false, bool MASKED = false>
 __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, const RobotSm& rb,
                                                  const SceneSm& m, const CollWarp& w,
                                                  const uint32_t* prow, const DevFmt& fP,
                                                  const DevFmt& fD, const DevFmt& fG, float eta,
                                                  float w_c, float w_s, const CollOut& out,
-                                                 int lane) {
+                                                 int lane, const float* est = nullptr,
+                                                 float margin = 0.f) {
   const int J = r.J, S = r.S, NP = r.NP;
   const unsigned lt_mask = (1u << lane) - 1u;
   // ---- 1. sphere centres (one word per lane)
@@ -298,15 +303,26 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
     });
   }
   __syncwarp();
+  if constexpr (MASKED) {
+    for (int s0 = 0; s0 < S; s0 += 32) {
+      const int s = s0 + lane;
+      const bool clear = s < S && __ldg(est + s) - w.P[s].w >= margin;
+      const unsigned bal = __ballot_sync(FULL_MASK, clear);
+      if (lane == 0) w.far[s0 >> 5] = bal;
+    }
+    __syncwarp();
+  }
   // ---- 2. link bounding spheres centred on the middle sphere of the link;
   //      radius = max |c_s - centre| + r_s (integer atomicMax on float bits)
   if (lane < J) {
     const int b = rb.start[lane], e = rb.start[lane + 1];
     const float4 ctr = e > b ? w.P[rb.order[b + (e - b) / 2]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    w.lb[lane] = make_float4(ctr.x, ctr.y, ctr.z, e > b ? 0.f : -1.f);
+    w.lb[lane] = make_float4(ctr.x, ctr.y, ctr.z, (e > b && !MASKED) ? 0.f : -1.f);
   }
   __syncwarp();
   for (int s = lane; s < S; s += 32) {
+    if constexpr (MASKED)
+      if ((w.far[s >> 5] >> (s & 31)) & 1u) continue;
     const float4 p = w.P[s];
     const float4 b = w.lb[rb.link0[s]];
     const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
@@ -362,6 +378,7 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
           const float dx = p.x - C.x, dy = p.y - C.y, dz = p.z - C.z;
           const float thr = p.w + C.w;
           nr = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < thr * thr;
+          if constexpr (MASKED) nr = nr && !((w.far[s >> 5] >> (s & 31)) & 1u);
         }
         const unsigned bal = __ballot_sync(FULL_MASK, nr);
         if (nr) w.queue[qn + __popc(bal & lt_mask)] = (uint32_t)s | ((uint32_t)o << 16);

@@ -8,8 +8,9 @@
 //   warp 1 lane 0  MMA issuer: four K=16 tcgen05.mma per slice into one
 //                  128 x 256 FP32 accumulator (256 TMEM columns), then
 //                  tcgen05.commit onto the slice's "empty" mbarrier;
-//   all 4 warps    epilogue: warp w reads TMEM lanes 32w..32w+31 (its 32
-//                  rows) with tcgen05.ld, 32 columns at a time.
+//   all 4 warps    epilogue: warp w owns TMEM lanes 32w..32w+31 (its 32
+//                  rows); the epilogue functor epi(taddr, row, n0, z) reads
+//                  them with tcgen05.ld (taddr = the warp's lane base).
 // Every mbarrier wait is bounded; on timeout the CTA records
 // VAPR_ERR_TIMEOUT, skips the rest, lets copies in flight land (bounded)
 // and frees its tensor memory.
@@ -105,13 +106,9 @@ __global__ void __launch_bounds__(128, 1)
   const bool ok = __all_sync(0xffffffffu, landed) && !*abort_flag;
   tc_fence_after();
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int c = 0; c < TG_N / 32; ++c) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-      epi(row, n0 + c * 32, r, (int)blockIdx.z);
-    }
+    // the epilogue reads its row's 256 accumulator columns from tensor memory
+    // (lane field = TMEM lane, column field = column) with tmem_ld32
+    epi(tmem + ((uint32_t)(warp * 32) << 16), m0 + warp * 32 + lane, n0, (int)blockIdx.z);
   } else if (lane == 0) {
     atomicCAS(err, 0, (int)VAPR_ERR_TIMEOUT);
   }
@@ -119,6 +116,25 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 256);
 }
+
+// Epilogue: FP32 rows of C (split z writes its own C slab).
+struct StoreF32 {
+  float* C;
+  int N;
+  int64_t slab;  // elements per split
+  __device__ __forceinline__ void operator()(uint32_t taddr, int row, int n0, int z) const {
+#pragma unroll 1
+    for (int c = 0; c < TG_N / 32; ++c) {
+      uint32_t r[32];
+      tmem_ld32(taddr + (uint32_t)(c * 32), r);
+      float4* out = reinterpret_cast<float4*>(C + z * slab + (int64_t)row * N + n0 + c * 32);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        out[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                             __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+    }
+  }
+};
 
 // Host: tensor map of a row-major bf16 matrix [rows][K] read in 64 x box_rows
 // tiles with 128-byte swizzle.  False if the driver rejects it.

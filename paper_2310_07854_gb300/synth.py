@@ -230,3 +230,44 @@ def make_uneven_problems(seed: int = 4, n_problems: int = 64):
                                  params=CostParams(), n_traj=n_traj,
                                  horizon=horizon))
     return problems
+
+
+# ------------------------------------------------------ surrogate training data
+def uniform_points(seed: int, lo, hi, n: int) -> np.ndarray:
+    """``n`` points uniform in the box [lo, hi]."""
+    rng = np.random.default_rng(seed + 5_000_011)
+    return rng.uniform(np.asarray(lo, np.float64), np.asarray(hi, np.float64), size=(n, 3)).astype(np.float32)
+
+
+def near_surface_points(seed: int, scene: Scene, n: int, sigma: float = 0.02) -> np.ndarray:
+    """``n`` points near cuboid surfaces: a cuboid drawn uniformly, a face
+    drawn by area, a point uniform on the face, then Gaussian noise of
+    ``sigma`` metres per axis."""
+    rng = np.random.default_rng(seed + 6_000_023)
+    O = scene.n_cuboids
+    R = scene.pose[:, :9].reshape(O, 3, 3).astype(np.float64)
+    t = scene.pose[:, 9:].astype(np.float64)
+    h = scene.half_ext.astype(np.float64)
+    o = rng.integers(0, O, size=n)
+    area = np.stack([h[:, 1] * h[:, 2], h[:, 0] * h[:, 2], h[:, 0] * h[:, 1]], 1)[o]
+    u = rng.uniform(0.0, 1.0, size=n) * area.sum(1)
+    axis = (u > area[:, 0]).astype(np.int64) + (u > area[:, 0] + area[:, 1]).astype(np.int64)
+    local = rng.uniform(-1.0, 1.0, size=(n, 3)) * h[o]
+    sign = np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)
+    local[np.arange(n), axis] = sign * h[o, axis]
+    world = t[o] + np.einsum("nij,nj->ni", R[o], local)
+    return (world + rng.normal(0.0, sigma, size=(n, 3))).astype(np.float32)
+
+
+def init_mlp_params(seed: int, hidden: int = 256, w1_scale: float = 4.0) -> np.ndarray:
+    """Initial surrogate parameters in the library's order (W1, b1, W2, b2,
+    W3, b3, w4, b4): W1 and b1 ~ N(0, w1_scale^2) so that the first-layer
+    hyperplanes cut the [-1, 1]^3 domain at many offsets, W2 and W3 ~
+    N(0, 2/hidden) (He), w4 ~ N(0, 1/hidden), other biases zero."""
+    rng = np.random.default_rng(seed + 7_000_003)
+    H = hidden
+    parts = [rng.normal(0.0, w1_scale, 3 * H), rng.normal(0.0, w1_scale, H),
+             rng.normal(0.0, np.sqrt(2.0 / H), H * H), np.zeros(H),
+             rng.normal(0.0, np.sqrt(2.0 / H), H * H), np.zeros(H),
+             rng.normal(0.0, np.sqrt(1.0 / H), H), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

@@ -149,3 +149,45 @@ def test_gemm_argument_checks():
     assert lib.vapr_gemm_bf16(256, 256, 256, 128, 256, 32, None) == 1   # K % 64
     assert lib.vapr_gemm_bf16(256, 256, 264, 128, 256, 64, None) == 3   # misaligned C
     assert lib.vapr_gemm_bf16(256, 256, 256, 0, 256, 64, None) == 0     # empty
+
+
+def test_surrogate_argument_checks():
+    """Bad arguments of the surrogate entry points return a status before
+    any CUDA call (fake device addresses are never dereferenced)."""
+    lib = B.lib()
+    assert lib.vapr_mlp_state_bytes() > 3 * 4 * B.MLP_PARAMS
+    assert lib.vapr_mlp_workspace_bytes(0) == 0
+    assert lib.vapr_mlp_workspace_bytes(100) == 0
+    assert lib.vapr_mlp_workspace_bytes(1 << 21) == 0
+    assert lib.vapr_mlp_workspace_bytes(128) > 0
+    assert lib.vapr_mlp_workspace_bytes(256) > lib.vapr_mlp_workspace_bytes(128)
+    st, p = 4096, 8192
+    assert lib.vapr_mlp_init(None, p, None) == 1
+    assert lib.vapr_mlp_init(st + 16, p, None) == 3
+    assert lib.vapr_mlp_forward(st, p, -1, p, None) == 1
+    assert lib.vapr_mlp_forward(st, p, 0, p, None) == 0
+    assert lib.vapr_mlp_forward(st, p + 2, 10, p, None) == 3
+    ws = lib.vapr_mlp_workspace_bytes(128)
+    assert lib.vapr_mlp_grads(st, p, p, 100, 1.0, st, ws, None, None, None) == 1
+    assert lib.vapr_mlp_grads(st, p, p, 128, 1.0, st, ws - 1, None, None, None) == 1
+    assert lib.vapr_mlp_grads(st, p, p, 128, 0.0, st, ws, None, None, None) == 1
+    assert lib.vapr_mlp_grads(st, p, p, 1 << 21, 1.0, st, ws, None, None, None) == 6
+    bad = B.vapr_train_params(1e-3, 1.0, 0.999, 1e-8, 1.0)
+    assert lib.vapr_mlp_train_step(st, p, p, 128, ctypes.byref(bad), st, ws, None, None) == 1
+    bad = B.vapr_train_params(1e-3, 0.9, 0.999, 1e-8, -1.0)
+    assert lib.vapr_mlp_train_step(st, p, p, 128, ctypes.byref(bad), st, ws, None, None) == 1
+    scene = B.vapr_scene(1, 0, 4096, 8192)
+    dom = B.surrogate_domain([0, 0, 0], [1, 1, 1], 0.1, 0.05)
+    assert lib.vapr_scene_sdf(ctypes.byref(scene), None, 5, p, None) == 1
+    assert lib.vapr_scene_sdf(ctypes.byref(scene), p, 0, p, None) == 0
+    flat = B.surrogate_domain([0, 0, 0], [1, 0, 1], 0.1, 0.05)
+    assert lib.vapr_surrogate_samples(ctypes.byref(scene), ctypes.byref(flat), p, 5, -1.0, 1.0, p, p,
+                                      None) == 1
+    assert lib.vapr_surrogate_samples(ctypes.byref(scene), ctypes.byref(dom), p, 5, 1.0, -1.0, p, p,
+                                      None) == 1
+    neg = B.surrogate_domain([0, 0, 0], [1, 1, 1], -0.1, 0.05)
+    assert lib.vapr_surrogate_samples(ctypes.byref(scene), ctypes.byref(neg), p, 5, -1.0, 1.0, p, p,
+                                      None) == 1
+    big = B.vapr_scene(B.MAX_CUBOIDS + 1, 0, 4096, 8192)
+    assert lib.vapr_surrogate_samples(ctypes.byref(big), ctypes.byref(dom), p, 5, -1.0, 1.0, p, p,
+                                      None) == 6

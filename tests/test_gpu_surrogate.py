@@ -1,0 +1,319 @@
+"""The learned signed-distance surrogate on the GPU: exact labels, the
+tcgen05 forward and backward kernels against the FP64 oracle network, the
+Adam step, and the gated collision stage (training, error against the exact
+kernel, and what the trained network gains over running without it).
+
+Tolerances.  The two hidden layers take bfloat16 operands (unit roundoff
+u = 2^-9) with float32 accumulation, and SiLU uses the hardware tanh
+(relative error ~2^-11).  Against an FP64 evaluation that rounds the same
+operands to bfloat16 (oracle bf16_activations with bf16-rounded W2, W3) the
+remaining differences are activations whose rounding falls the other way
+(one bfloat16 step, 2u, on a fraction of the 512 hidden values) and the
+float32 sums: 1e-2 of max|f| normwise.  Against the unrounded FP64 network
+and its gradient, the operand rounding itself enters: 3e-2 normwise for f,
+6e-2 per parameter block for the gradient (cosine >= 0.998); the scalar db4,
+a cancelling sum of residuals, within 3e-2 of the mean |summand|.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_07854_gb300 import binding as B
+from paper_2310_07854_gb300 import formats as F
+from paper_2310_07854_gb300 import surrogate as SG
+from paper_2310_07854_gb300 import synth
+from parity import to_dev
+
+pytestmark = pytest.mark.gpu
+
+H = 256
+BLOCKS = {"W1": (0, 3 * H), "b1": (3 * H, H), "W2": (4 * H, H * H), "b2": (4 * H + H * H, H),
+          "W3": (5 * H + H * H, H * H), "b3": (5 * H + 2 * H * H, H),
+          "w4": (6 * H + 2 * H * H, H), "b4": (7 * H + 2 * H * H, 1)}
+
+
+def _bf16_weights(p):
+    q = p.copy()
+    for k in ("W2", "W3"):
+        o, n = BLOCKS[k]
+        q[o:o + n] = oracle.quantize(p[o:o + n], 8, 7).astype(np.float32)
+    return q
+
+
+def _state(params):
+    import torch
+    st = B.alloc_mlp_state()
+    B.vapr_mlp_init(st, torch.as_tensor(params, device="cuda"))
+    return st
+
+
+def _normwise(got, want):
+    return float(np.max(np.abs(got - want)) / max(np.max(np.abs(want)), 1e-30))
+
+
+# ------------------------------------------------------------- exact labels
+def test_scene_sdf_matches_oracle():
+    import torch
+    scene = synth.make_scene(3, 40)
+    ds = B.DeviceScene(scene)
+    lo, hi = SG.domain_box(scene)
+    pts = np.concatenate([synth.uniform_points(1, lo - 0.5, hi + 0.5, 6000),
+                          synth.near_surface_points(1, scene, 6000)])
+    out = torch.empty(len(pts), device="cuda")
+    B.vapr_scene_sdf(ds, to_dev(pts), len(pts), out)
+    want = oracle.scene_sdf(scene, pts)
+    assert np.max(np.abs(out.cpu().numpy() - want)) <= 4e-6
+
+
+def test_samples_coordinates_and_labels():
+    import torch
+    scene = synth.make_scene(5, 12)
+    ds = B.DeviceScene(scene)
+    sg = SG.Surrogate(ds, synth.init_mlp_params(0))
+    pts = synth.uniform_points(2, sg.lo, sg.hi, 1000)
+    u, y = sg.samples(pts)
+    u = u.cpu().numpy()
+    ctr, half = (sg.lo + sg.hi) / 2, (sg.hi - sg.lo) / 2
+    assert np.allclose(u, (pts - ctr) / half, atol=2e-6)
+    assert np.all(np.abs(u) <= 1 + 1e-6)
+    want = oracle.scene_sdf(scene, pts)
+    assert np.max(np.abs(y.cpu().numpy() - want)) <= 4e-6
+    _, yc = sg.samples(pts, -0.05, 0.1)
+    assert np.max(np.abs(yc.cpu().numpy() - np.clip(want, -0.05, 0.1))) <= 4e-6
+
+
+def test_empty_scene_sdf_is_max_float():
+    import torch
+    ds = B.DeviceScene(synth.make_scene(0, 0))
+    out = torch.zeros(5, device="cuda")
+    B.vapr_scene_sdf(ds, to_dev(np.zeros((5, 3), np.float32)), 5, out)
+    assert np.all(out.cpu().numpy() == np.finfo(np.float32).max)
+
+
+# ----------------------------------------------------------------- network
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 128 * 152 * 2 + 77])
+def test_forward_matches_oracle(n):
+    import torch
+    p = synth.init_mlp_params(11)
+    u = np.random.default_rng(n).uniform(-1, 1, (n, 3)).astype(np.float32)
+    st = _state(p)
+    out = torch.full((n,), np.nan, device="cuda")
+    B.vapr_mlp_forward(st, to_dev(u), n, out)
+    got = out.cpu().numpy().astype(np.float64)
+    m = min(n, 4000)  # the oracle on a sample of the rows (spread over tiles)
+    idx = np.unique(np.linspace(0, n - 1, m).astype(np.int64))
+    want_bf = oracle.mlp_forward(_bf16_weights(p), u[idx], H, bf16_activations=True)
+    want = oracle.mlp_forward(p, u[idx], H)
+    assert np.all(np.isfinite(got))
+    assert _normwise(got[idx], want_bf) <= 1e-2
+    assert _normwise(got[idx], want) <= 3e-2
+
+
+def test_forward_is_deterministic_and_batch_independent():
+    import torch
+    p = synth.init_mlp_params(12)
+    st = _state(p)
+    u = to_dev(np.random.default_rng(0).uniform(-1, 1, (5000, 3)).astype(np.float32))
+    a = torch.empty(5000, device="cuda")
+    b = torch.empty(5000, device="cuda")
+    B.vapr_mlp_forward(st, u, 5000, a)
+    B.vapr_mlp_forward(st, u[1000:], 4000, b[1000:])
+    B.vapr_mlp_forward(st, u[:1000], 1000, b[:1000])
+    assert torch.equal(a, b)
+    assert B.vapr_device_error() == 0
+
+
+@pytest.mark.parametrize("batch,ow", [(128, 1.0), (384, 1.0), (256, 4.0)])
+def test_gradients_match_oracle(batch, ow):
+    import torch
+    p = synth.init_mlp_params(13, w1_scale=2.0)
+    rng = np.random.default_rng(batch)
+    u = rng.uniform(-1, 1, (batch, 3)).astype(np.float32)
+    y = rng.uniform(-0.5, 0.5, batch).astype(np.float32)
+    st = _state(p)
+    ws = B.alloc_mlp_workspace(batch)
+    g = torch.empty(B.MLP_PARAMS, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    B.vapr_mlp_grads(st, to_dev(u), to_dev(y), batch, ws, g, loss, over_weight=ow)
+    want_loss, want = oracle.mlp_grads(p, u, y, H, over_weight=ow)
+    got = g.cpu().numpy().astype(np.float64)
+    assert float(loss) == pytest.approx(want_loss, rel=3e-2)
+    for k, (o, m) in BLOCKS.items():
+        a, b = got[o:o + m], want[o:o + m]
+        if m > 1:
+            assert _normwise(a, b) <= 6e-2, k
+            cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+            assert cos >= 0.998, (k, cos)
+        else:
+            # db4 = (2/n) sum_i r_i cancels; its error is measured against the
+            # size of the summands, mean |2 r_i|
+            r = oracle.mlp_forward(p, u, H) - y
+            wr = np.where(r > 0, ow, 1.0) * r
+            assert abs(a[0] - b[0]) <= 3e-2 * np.mean(np.abs(2 * wr)), (a[0], b[0])
+    # determinism
+    g2 = torch.empty_like(g)
+    B.vapr_mlp_grads(st, to_dev(u), to_dev(y), batch, ws, g2, None, over_weight=ow)
+    assert torch.equal(g, g2)
+
+
+def test_adam_step():
+    """One step from zero moments: p - lr * g / (|g| + eps) per parameter
+    (bias correction makes m_hat = g and v_hat = g^2 at step 1)."""
+    import torch
+    p = synth.init_mlp_params(14)
+    rng = np.random.default_rng(3)
+    batch = 256
+    u = to_dev(rng.uniform(-1, 1, (batch, 3)).astype(np.float32))
+    y = to_dev(rng.uniform(-0.5, 0.5, batch).astype(np.float32))
+    st = _state(p)
+    ws = B.alloc_mlp_workspace(batch)
+    g = torch.empty(B.MLP_PARAMS, device="cuda")
+    B.vapr_mlp_grads(st, u, y, batch, ws, g, None)
+    lr, eps = 1e-3, 1e-8
+    B.vapr_mlp_train_step(st, u, y, batch, (lr, 0.9, 0.999, eps), ws)
+    newp = torch.empty(B.MLP_PARAMS, device="cuda")
+    B.vapr_mlp_get_params(st, newp)
+    gh = g.cpu().numpy().astype(np.float64)
+    want = p.astype(np.float64) - lr * gh / (np.abs(gh) + eps)
+    assert np.max(np.abs(newp.cpu().numpy() - want)) <= 1e-6
+    # the bf16 copies follow the master weights: forward equals a fresh init
+    st2 = _state(newp.cpu().numpy())
+    uu = to_dev(rng.uniform(-1, 1, (512, 3)).astype(np.float32))
+    a, b = torch.empty(512, device="cuda"), torch.empty(512, device="cuda")
+    B.vapr_mlp_forward(st, uu, 512, a)
+    B.vapr_mlp_forward(st2, uu, 512, b)
+    assert torch.equal(a, b)
+
+
+# --------------------------------------------------- gated collision stage
+def _pos_fp32(w, rd):
+    import torch
+    q = to_dev(w.q)
+    pos = B.alloc_packed(w.n, 3 * w.robot.n_spheres, F.FP32)
+    B.vapr_fk(rd, q, w.n, F.FP32_TABLE, pos)
+    return pos
+
+
+def _exact(w, rd, sd, pos):
+    import torch
+    S = w.robot.n_spheres
+    cost = torch.empty(w.n, device="cuda")
+    dist = B.alloc_packed(w.n, S, F.FP32)
+    grad = B.alloc_packed(w.n, 3 * S, F.FP32)
+    B.vapr_collision_cost(rd, sd, w.params, pos, w.n, F.FP32_TABLE, cost, dist, grad)
+    return cost, dist, grad
+
+
+def _gated(sg, w, rd, pos):
+    import torch
+    S = w.robot.n_spheres
+    cost = torch.empty(w.n, device="cuda")
+    dist = B.alloc_packed(w.n, S, F.FP32)
+    grad = B.alloc_packed(w.n, 3 * S, F.FP32)
+    est = sg.collision_cost(rd, w.params, pos, w.n, F.FP32_TABLE, cost, dist, grad)
+    return cost, dist, grad, est
+
+
+def test_gate_off_equals_exact_path():
+    """margin = +inf: no sphere skips the exact test, whatever the network."""
+    import torch
+    w = synth.make_workload("sweep_1024")
+    rd, sd = B.DeviceRobot(w.robot), B.DeviceScene(w.scene)
+    sg = SG.Surrogate(sd, synth.init_mlp_params(1), margin=1e30)
+    pos = _pos_fp32(w, rd)
+    e = _exact(w, rd, sd, pos)
+    g = _gated(sg, w, rd, pos)
+    for a, b in zip(e, g[:3]):
+        assert torch.equal(a, b)
+
+
+def test_estimate_semantics():
+    """Inside the domain box the estimate is the network at the sphere
+    centre; outside it is dist(c, box) + pad, a lower bound of sdf(c)."""
+    import torch
+    w = synth.make_workload("sweep_1024")
+    w.scene = synth.make_scene(7, 6, extent=0.25)  # a small box: many spheres outside it
+    rd, sd = B.DeviceRobot(w.robot), B.DeviceScene(w.scene)
+    sg = SG.Surrogate(sd, synth.init_mlp_params(2))
+    pos = _pos_fp32(w, rd)
+    est = _gated(sg, w, rd, pos)[3].cpu().numpy().reshape(-1)
+    c = pos.view(torch.float32)[:, :3 * w.robot.n_spheres].reshape(-1, 3).contiguous()
+    cn = c.cpu().numpy()
+    inside = np.all((cn >= sg.lo) & (cn <= sg.hi), axis=1)
+    assert inside.any() and (~inside).any()
+    u, y = sg.samples(c)
+    f = sg.forward(u).cpu().numpy()
+    assert np.array_equal(est[inside], f[inside])
+    exact = oracle.scene_sdf(w.scene, cn[~inside])
+    assert np.all(est[~inside] <= exact)
+    e64 = np.linalg.norm(np.maximum(np.maximum(sg.lo - cn[~inside], cn[~inside] - sg.hi), 0), axis=1) + SG.PAD
+    assert np.max(np.abs(est[~inside] - e64)) <= 1e-5
+
+
+def test_trained_surrogate_config5():
+    """Trains on 2M exact distances of the 40-cuboid scene, then gates the
+    exact test for the 1024 x 32 x 52 sphere queries.  Checks that training
+    converges, that no sphere the network clears is within eta of a surface
+    (so cost, D and G equal the exact path bit for bit), and what the
+    trained network gains over the same network untrained: the share of
+    spheres it clears safely."""
+    import torch
+    w = synth.make_workload("particle_32768")
+    S, eta = w.robot.n_spheres, w.params.eta
+    rd, sd = B.DeviceRobot(w.robot), B.DeviceScene(w.scene)
+    pos = _pos_fp32(w, rd)
+    c = pos.view(torch.float32)[:, :3 * S].reshape(-1, 3).contiguous()
+    r = to_dev(np.tile(w.robot.sphere_local[:, 3], w.n))
+    sdf = torch.empty(w.n * S, device="cuda")
+    B.vapr_scene_sdf(sd, c, w.n * S, sdf)
+    exact = _exact(w, rd, sd, pos)
+
+    def evaluate(sg):
+        cost, dist, grad, est = _gated(sg, w, rd, pos)
+        est = est.reshape(-1)
+        skipped = (est - r) >= sg.domain.margin
+        miss = skipped & (sdf < r + eta)
+        u, _ = sg.samples(c)
+        inside = (u.abs() <= 1).all(1)
+        band = inside & (sdf >= SG.Y_MIN) & (sdf <= SG.Y_MAX)
+        err = (est - sdf).abs()
+        errc = (est.clamp(SG.Y_MIN, SG.Y_MAX) - sdf.clamp(SG.Y_MIN, SG.Y_MAX)).abs()
+        return {
+            "cleared": float(skipped.float().mean()),
+            "clearable": float(((sdf - r) >= sg.domain.margin).float().mean()),
+            "misses": int(miss.sum()),
+            "max_err_band": float(err[band].max()),
+            "rms_err_band": float(err[band].square().mean().sqrt()),
+            "max_err_clamped_inside": float(errc[inside].max()),
+            "max_overestimate_band": float((est - sdf)[band].max()),
+            "inside_fraction": float(inside.float().mean()),
+            "equal_to_exact": all(torch.equal(a, b) for a, b in zip(exact, (cost, dist, grad))),
+        }
+
+    p0 = synth.init_mlp_params(5)
+    untrained = evaluate(SG.Surrogate(sd, p0))
+    sg = SG.Surrogate(sd, p0)
+    u, y = sg.training_set(seed=5)
+    losses = sg.train(u, y, epochs=int(os.environ.get("VAPR_SURROGATE_EPOCHS", "80")))
+    del u, y
+    nominal = evaluate(sg)  # the 0.05 m margin
+    delta = sg.calibrate(seed=99, eta=eta)
+    trained = evaluate(sg)  # margin from the validation overestimate
+    report = {"losses": losses, "untrained": untrained, "trained_nominal_margin": nominal,
+              "validation_max_overestimate": delta, "margin": sg.domain.margin, "trained": trained}
+    print(json.dumps(report))
+    out_dir = os.environ.get("VAPR_REPORT_DIR")
+    if out_dir:
+        with open(os.path.join(out_dir, "surrogate_config5.json"), "w") as fh:
+            json.dump(report, fh)
+    assert losses[-1] < 1e-2 * losses[0]
+    # the gain: the trained network clears a share of the spheres with no
+    # missed contact (results bit-equal to the exact stage); the untrained
+    # one clears almost everything and misses contacts
+    assert trained["misses"] == 0 and trained["equal_to_exact"]
+    assert untrained["misses"] > 0 and not untrained["equal_to_exact"]
+    assert trained["cleared"] >= 0.5 * trained["clearable"]
+    assert B.vapr_device_error() == 0
