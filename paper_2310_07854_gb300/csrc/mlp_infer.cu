@@ -2,23 +2,28 @@
 // launch, the exact scene distance that labels its training data, and the
 // collision stage with the network as a broad phase.
 //
-// mlp_infer_kernel, one CTA per SM, 10 warps:
-//   warp 8 lane 0   TMA producer: streams 64-column K slices of W2 and W3
-//                   (256 x 64 bf16, 128-byte swizzled) through a 3-stage
-//                   ring, eight slices per tile, for every tile of the CTA;
-//   warp 9 lane 0   MMA issuer: per layer, waits until the activations are
-//                   in shared memory, issues 16 tcgen05.mma (M=128, N=256,
-//                   K=16) into one 128 x 256 FP32 accumulator (256 TMEM
-//                   columns), frees ring slots with tcgen05.commit and
-//                   signals the accumulator;
-//   warps 0-7       per tile of 128 inputs: layer 1 (3 -> 256, CUDA cores)
-//                   written as bf16 straight into the swizzled A operand;
-//                   the layer-2 epilogue (bias, SiLU, bf16) writes A again in
-//                   place; the layer-3 epilogue does bias, SiLU and the dot
-//                   product with w4.  Warp w reads TMEM lanes 32(w%4).. (its
-//                   rows) and columns 128(w/4).. (its half).
-// The activations never leave the SM; only the weights (from L2) and the 12
-// input and 4 output bytes per query touch memory.
+// mlp_infer_kernel, one CTA per SM, 10 warps, two tiles of 128 inputs in
+// flight so that the CUDA-core work of one overlaps the tensor-core work of
+// the other:
+//   warp 8 lane 0   TMA producer: streams 16 KB weight slices (128 output
+//                   units x 64 inputs of W2 or W3, 128-byte swizzled)
+//                   through a 5-stage ring, 16 slices per tile, for every
+//                   tile of the CTA;
+//   warp 9 lane 0   MMA issuer: layer 2 of tile t (A1 x W2^T into TMEM
+//                   columns 0-255, one N=128 half at a time), then layer 3
+//                   (A2 x W3^T into columns 256-511); each half is
+//                   signalled with tcgen05.commit;
+//   warps 0-7       per tile: layer 1 (3 -> 256, CUDA cores) into the
+//                   swizzled A1 operand; the layer-2 epilogue (bias, SiLU,
+//                   bf16) into A2; the layer-3 epilogue (bias, SiLU, dot
+//                   with w4).  Warp w reads TMEM lanes 32(w%4).. (its rows)
+//                   and the column half w/4.
+// Order of the compute warps: epi2(t), L1(t+1), epi3(t), so that layer 3 of
+// tile t runs under L1(t+1) and layer 2 of tile t+1 under epi3(t).
+// Buffers: A1 (written by L1, read by layer 2), A2 (epi2 / layer 3), the two
+// TMEM accumulators; each is reused only after the commit that ends its
+// last reader.  The activations never leave the SM; only the weights (from
+// L2) and 12 input and 4 output bytes per query touch memory.
 // Waits are bounded.  On a timeout the CTA records VAPR_ERR_TIMEOUT and runs
 // to its end without waiting again (compute warps still pass every named
 // barrier, so none is left behind), lets its copies and MMAs land, and frees
@@ -29,14 +34,13 @@
 
 namespace vapr {
 
-constexpr int MI_STAGES = 3;
+constexpr int MI_STAGES = 5;
 constexpr int MI_CWARPS = 8;
 constexpr int MI_THREADS = (MI_CWARPS + 2) * 32;
-constexpr uint32_t MI_SLICE = 128 * 128;      // one K slice of A: 128 rows x 128 B
-constexpr uint32_t MI_A_BYTES = 4 * MI_SLICE; // 128 x 256 bf16
-constexpr uint32_t MI_W_BYTES = MH * TG_K * 2; // 256 x 64 bf16
-constexpr size_t MI_SMEM = 1024 + MI_A_BYTES + MI_STAGES * MI_W_BYTES + 2 * 128 * 16 +
-                           3 * MH * 4 + 2 * 128 * 4 + 16 * 8 + 16;
+constexpr uint32_t MI_SLICE = 128 * 128;       // 128 rows x 64 bf16 (128 B), swizzled
+constexpr uint32_t MI_A_BYTES = 4 * MI_SLICE;  // 128 x 256 bf16 activations
+constexpr size_t MI_SMEM = 1024 + 2 * MI_A_BYTES + MI_STAGES * MI_SLICE + 3 * 128 * 16 +
+                           3 * MH * 4 + 2 * 128 * 4 + 24 * 8 + 16;
 
 __device__ __forceinline__ void cw_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() {
@@ -90,18 +94,21 @@ __global__ void __launch_bounds__(MI_THREADS, 1)
                      const float* __restrict__ p, In in, int64_t n, float* __restrict__ out, int* err) {
   extern __shared__ uint8_t mi_raw[];
   uint8_t* base = mi_raw + ((1024u - (sm_addr(mi_raw) & 1023u)) & 1023u);
-  uint8_t* sA = base;
-  uint8_t* ring = base + MI_A_BYTES;
-  float4* xin = reinterpret_cast<float4*>(ring + MI_STAGES * MI_W_BYTES);  // [2][128]
-  float* sb2 = reinterpret_cast<float*>(xin + 2 * 128);
+  uint8_t* sA1 = base;
+  uint8_t* sA2 = base + MI_A_BYTES;
+  uint8_t* ring = base + 2 * MI_A_BYTES;
+  float4* xin = reinterpret_cast<float4*>(ring + MI_STAGES * MI_SLICE);  // [3][128]
+  float* sb2 = reinterpret_cast<float*>(xin + 3 * 128);
   float* sb3 = sb2 + MH;
   float* sw4 = sb3 + MH;
   float* red = sw4 + MH;  // [2][128]
   uint64_t* full = reinterpret_cast<uint64_t*>(red + 2 * 128);
   uint64_t* empty = full + MI_STAGES;
-  uint64_t* a_full = empty + MI_STAGES;
-  uint64_t* acc_full = a_full + 1;
-  uint64_t* drain = acc_full + 1;
+  uint64_t* a1_full = empty + MI_STAGES;  // L1(t) written (256 arrivals)
+  uint64_t* a2_full = a1_full + 1;        // epi2(t) done (256 arrivals)
+  uint64_t* acc2 = a2_full + 1;           // [2] layer-2 half done
+  uint64_t* acc3 = acc2 + 2;              // [2] layer-3 half done
+  uint64_t* drain = acc3 + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -114,8 +121,12 @@ __global__ void __launch_bounds__(MI_THREADS, 1)
       mb_init(full + s, 1);
       mb_init(empty + s, 1);
     }
-    mb_init(a_full, MI_CWARPS * 32);
-    mb_init(acc_full, 1);
+    mb_init(a1_full, MI_CWARPS * 32);
+    mb_init(a2_full, MI_CWARPS * 32);
+    for (int h = 0; h < 2; ++h) {
+      mb_init(acc2 + h, 1);
+      mb_init(acc3 + h, 1);
+    }
     mb_init(drain, 1);
     *abort_flag = 0;
     mb_init_fence();
@@ -125,16 +136,16 @@ __global__ void __launch_bounds__(MI_THREADS, 1)
     sb3[i] = p[OFF_B3 + i];
     sw4[i] = p[OFF_W4 + i];
   }
-  if (warp == 0) tmem_alloc(tslot, 256);
+  if (warp == 0) tmem_alloc(tslot, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t IDESC = idesc_bf16_f32(128, MH);
+  constexpr uint32_t IDESC = idesc_bf16_f32(128, 128);
 
   if (warp == MI_CWARPS) {  // ---- TMA producer
     if (lane == 0) {
-      const int total = my_tiles * 8;
+      const int total = my_tiles * 16;
       int issued = 0;
       for (int it = 0; it < total; ++it) {
         const int s = it % MI_STAGES;
@@ -143,8 +154,10 @@ __global__ void __launch_bounds__(MI_THREADS, 1)
           break;
         }
         if (*abort_flag) break;
-        mb_expect_tx(full + s, MI_W_BYTES);
-        tma_load_2d(ring + s * MI_W_BYTES, (it & 4) ? &tmW3 : &tmW2, (it & 3) * TG_K, 0, full + s);
+        mb_expect_tx(full + s, MI_SLICE);
+        const int j = it & 15;  // layer (j >> 3), output half ((j >> 2) & 1), K slice (j & 3)
+        tma_load_2d(ring + s * MI_SLICE, (j & 8) ? &tmW3 : &tmW2, (j & 3) * TG_K, ((j >> 2) & 1) * 128,
+                    full + s);
         issued = it + 1;
       }
       if (*abort_flag)  // let every issued copy land before the CTA can exit
@@ -154,30 +167,32 @@ __global__ void __launch_bounds__(MI_THREADS, 1)
     __syncwarp();
   } else if (warp == MI_CWARPS + 1) {  // ---- MMA issuer
     if (lane == 0) {
-      int it = 0, ph = 0;
+      int it = 0;
       bool ok = true;
       for (int t = 0; t < my_tiles && ok; ++t) {
         for (int layer = 0; layer < 2 && ok; ++layer) {
-          if (!mb_wait(a_full, ph & 1, TG_WAIT) || *abort_flag) {
+          if (!mb_wait(layer ? a2_full : a1_full, t & 1, TG_WAIT) || *abort_flag) {
             ok = false;
             break;
           }
-          ++ph;
           tc_fence_after();
-          for (int ks = 0; ks < 4; ++ks, ++it) {
-            const int s = it % MI_STAGES;
-            if (!mb_wait(full + s, (it / MI_STAGES) & 1, TG_WAIT)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint64_t ad = sw128_desc(sA + ks * MI_SLICE), bd = sw128_desc(ring + s * MI_W_BYTES);
+          const uint8_t* sA = layer ? sA2 : sA1;
+          for (int nh = 0; nh < 2 && ok; ++nh) {
+            const uint32_t d = tmem + (uint32_t)(layer * 256 + nh * 128);
+            for (int ks = 0; ks < 4; ++ks, ++it) {
+              const int s = it % MI_STAGES;
+              if (!mb_wait(full + s, (it / MI_STAGES) & 1, TG_WAIT)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint64_t ad = sw128_desc(sA + ks * MI_SLICE), bd = sw128_desc(ring + s * MI_SLICE);
 #pragma unroll
-            for (int kk = 0; kk < TG_K / 16; ++kk)
-              umma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, IDESC, (ks | kk) != 0);
-            umma_commit(empty + s);
+              for (int kk = 0; kk < TG_K / 16; ++kk) umma_bf16(d, ad + 2 * kk, bd + 2 * kk, IDESC, (ks | kk) != 0);
+              umma_commit(empty + s);
+            }
+            if (ok) umma_commit((layer ? acc3 : acc2) + nh);
           }
-          if (ok) umma_commit(acc_full);
         }
       }
       if (!ok) *abort_flag = 1;
@@ -201,38 +216,42 @@ __global__ void __launch_bounds__(MI_THREADS, 1)
     const int rr = 32 * qd + lane;  // this thread's row in the epilogues
     const uint32_t trow = tmem + ((uint32_t)(32 * qd) << 16);
     bool failed = false;
-    int acc_ph = 0;
-    for (int t = 0; t < my_tiles; ++t) {
+    // bounded wait on a phase; once one wait has failed, none waits again
+    auto wait = [&](uint64_t* bar, int parity) {
+      if (!failed) failed = !mb_wait(bar, (uint32_t)parity, TG_WAIT);
+      failed = __any_sync(0xffffffffu, failed);
+      tc_fence_after();
+    };
+    // stage the inputs of tile t, then layer 1 into A1 (rows warp, warp+8, ...;
+    // lane = one 16-byte chunk of 8 columns)
+    auto layer1 = [&](int t) {
       const int64_t q0 = ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * 128;
-      float4* xt = xin + (t & 1) * 128;
-      float* rt = red + (t & 1) * 128;
+      float4* xt = xin + (t % 3) * 128;
       if (tid < 128) xt[tid] = q0 + tid < n ? in(q0 + tid) : make_float4(0.f, 0.f, 0.f, -1.f);
       cw_bar();
-      // layer 1: warp handles rows warp, warp+8, ...; lane = 16-byte chunk (8 columns)
-      {
-        const int slice = lane >> 3, ch = lane & 7;
+      const int slice = lane >> 3, ch = lane & 7;
 #pragma unroll 2
-        for (int r = warp; r < 128; r += MI_CWARPS) {
-          const float4 x = xt[r];
-          uint32_t a[4];
+      for (int r = warp; r < 128; r += MI_CWARPS) {
+        const float4 x = xt[r];
+        uint32_t a[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float z0 = fmaf(w1[2 * j][0], x.x, fmaf(w1[2 * j][1], x.y, fmaf(w1[2 * j][2], x.z, b1[2 * j])));
-            const float z1 = fmaf(w1[2 * j + 1][0], x.x,
-                                  fmaf(w1[2 * j + 1][1], x.y, fmaf(w1[2 * j + 1][2], x.z, b1[2 * j + 1])));
-            a[j] = pack_bf16x2(silu(z0), silu(z1));
-          }
-          *reinterpret_cast<uint4*>(sA + slice * MI_SLICE + r * 128 + ((ch ^ (r & 7)) << 4)) =
-              make_uint4(a[0], a[1], a[2], a[3]);
+        for (int j = 0; j < 4; ++j) {
+          const float z0 = fmaf(w1[2 * j][0], x.x, fmaf(w1[2 * j][1], x.y, fmaf(w1[2 * j][2], x.z, b1[2 * j])));
+          const float z1 = fmaf(w1[2 * j + 1][0], x.x,
+                                fmaf(w1[2 * j + 1][1], x.y, fmaf(w1[2 * j + 1][2], x.z, b1[2 * j + 1])));
+          a[j] = pack_bf16x2(silu(z0), silu(z1));
         }
+        *reinterpret_cast<uint4*>(sA1 + slice * MI_SLICE + r * 128 + ((ch ^ (r & 7)) << 4)) =
+            make_uint4(a[0], a[1], a[2], a[3]);
       }
       proxy_fence();
-      mb_arrive(a_full);
-      // layer-2 epilogue: + b2, SiLU, bf16 back into A (the MMAs reading it are done)
-      if (!failed) failed = !mb_wait(acc_full, acc_ph & 1, TG_WAIT);
-      failed = __any_sync(0xffffffffu, failed);
-      ++acc_ph;
-      tc_fence_after();
+      mb_arrive(a1_full);
+    };
+    if (my_tiles > 0) layer1(0);
+    for (int t = 0; t < my_tiles; ++t) {
+      const int64_t q0 = ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * 128;
+      // ---- epi2(t): + b2, SiLU, bf16 into A2 (free: layer 3 of t-1 is done)
+      wait(acc2 + half, t & 1);
       if (!failed) {
 #pragma unroll 1
         for (int c = 0; c < 4; ++c) {
@@ -244,7 +263,7 @@ __global__ void __launch_bounds__(MI_THREADS, 1)
           for (int j = 0; j < 16; ++j)
             a[j] = pack_bf16x2(silu(__uint_as_float(r[2 * j]) + sb2[col0 + 2 * j]),
                                silu(__uint_as_float(r[2 * j + 1]) + sb2[col0 + 2 * j + 1]));
-          uint8_t* rowp = sA + (col0 >> 6) * MI_SLICE + rr * 128;
+          uint8_t* rowp = sA2 + (col0 >> 6) * MI_SLICE + rr * 128;
           const int ch0 = (col0 & 63) >> 3;
 #pragma unroll
           for (int k = 0; k < 4; ++k)
@@ -254,37 +273,42 @@ __global__ void __launch_bounds__(MI_THREADS, 1)
       }
       tc_fence_before();
       proxy_fence();
-      mb_arrive(a_full);
-      // layer-3 epilogue: + b3, SiLU, dot with w4; the two column halves meet in red
-      if (!failed) failed = !mb_wait(acc_full, acc_ph & 1, TG_WAIT);
-      failed = __any_sync(0xffffffffu, failed);
-      ++acc_ph;
-      tc_fence_after();
+      mb_arrive(a2_full);
+      // ---- L1(t+1) into A1 (free once both halves of layer 2 of t are done)
+      if (t + 1 < my_tiles) {
+        wait(acc2 + 1, t & 1);
+        layer1(t + 1);
+      }
+      // ---- epi3(t): + b3, SiLU, dot with w4; the two halves meet in red
+      wait(acc3 + half, t & 1);
       float part = 0.f;
       if (!failed) {
 #pragma unroll 1
         for (int c = 0; c < 4; ++c) {
           const int col0 = 128 * half + 32 * c;
           uint32_t r[32];
-          tmem_ld32(trow + (uint32_t)col0, r);
+          tmem_ld32(trow + (uint32_t)(256 + col0), r);
 #pragma unroll
           for (int j = 0; j < 32; ++j)
             part = fmaf(sw4[col0 + j], silu(__uint_as_float(r[j]) + sb3[col0 + j]), part);
         }
       }
       tc_fence_before();
+      float* rt = red + (t & 1) * 128;
       if (half == 1) rt[rr] = part;
       cw_bar();
       if (half == 0 && q0 + rr < n) {
-        const float lb = xt[rr].w;
+        const float lb = xin[(t % 3) * 128 + rr].w;
         out[q0 + rr] = lb >= 0.f ? lb : (b4 + part) + rt[rr];
       }
+      // A2 is rewritten by epi2(t+1): both halves of layer 3 of t must be done
+      wait(acc3 + 1, t & 1);
     }
     if (failed && lane == 0) atomicCAS(err, 0, (int)VAPR_ERR_TIMEOUT);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 256);
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 template <class In>
@@ -293,7 +317,7 @@ static cudaError_t launch_infer(const MlpState& s, In in, int64_t n, float* out,
   int* err = tc_error_word();
   if (!err) return cudaErrorUnknown;
   CUtensorMap m2, m3;
-  if (!tg_tensor_map(&m2, s.W2, MH, MH, MH) || !tg_tensor_map(&m3, s.W3, MH, MH, MH))
+  if (!tg_tensor_map(&m2, s.W2, MH, MH, 128) || !tg_tensor_map(&m3, s.W3, MH, MH, 128))
     return cudaErrorInvalidValue;
   const int per_sm = blocks_per_sm((const void*)mlp_infer_kernel<In>, MI_THREADS, MI_SMEM);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
