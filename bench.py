@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the learned-surrogate leg (training + gated collision)")
     ap.add_argument("--surrogate-epochs", type=int, default=80)
+    ap.add_argument("--no-search", action="store_true", help="skip the VaPr format search leg")
+    ap.add_argument("--search-samples", type=int, default=300)
     ap.add_argument("--configs", type=int, default=0,
                     help="override the batch size (configurations per GPU)")
     return ap.parse_args()
@@ -211,6 +213,65 @@ def kernel_traffic(stage: str, table: str):
     if not ent or ent.get("source_sha") != h:
         return None
     return ent.get("dram_bytes_per_config")
+
+
+def collision_flops_per_config(w) -> int:
+    """Algorithmic FP32 work of the collision stage per configuration: the
+    bounding test of every sphere/cuboid pair (|c - t|^2 < (r + R)^2: 3 sub,
+    1 mul, 2 fma, 1 add, 1 mul = 10 FLOP) and of every self pair (3 sub,
+    1 mul, 2 fma, 1 mul = 9 FLOP).  Exact distances of the pairs that pass
+    come on top; they are data-dependent and not counted."""
+    return 10 * w.robot.n_spheres * w.scene.n_cuboids + 9 * w.robot.n_pairs
+
+
+def fp32_peak_tflops(peaks) -> float:
+    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x max SM clock."""
+    return 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def search_leg(w, ev32, q, n, args, flush, torch, per32):
+    """VaPr search (Sec. V-A) for the workload: per-tensor binary search and
+    the combinatorial search on a 1024-configuration validation batch with a
+    5 % budget on C and J against the FP32 path, then the found table timed
+    on the full workload next to FP32."""
+    from paper_2310_07854_gb300 import search as S
+    from paper_2310_07854_gb300.path import Evaluator
+    tensors = ("pos", "dist", "grad", "jgrad")
+    t0 = time.perf_counter()
+    ev = S.CachedEvaluator(S.PathEvaluator(ev32.robot, ev32.scene, w.params, synth.make_q(901, 1024)))
+    per = S.per_tensor_search(ev, tensors)
+    space = S.reduced_space(per)
+    start = F.FormatTable(**{k: space[k][0] for k in tensors})
+    best, e, _ = S.combinatorial_search(ev, space, samples=args.search_samples, seed=0, seeds=[start])
+    search_s = time.perf_counter() - t0
+    out = {"budget": "max|C-C32| <= 5% max|C32| and max|J-J32| <= 5% max|J32| (1024 validation configs)",
+           "per_tensor_min_bits": {k: v[0] for k, v in per.items()}, "reduced_space": S.space_size(space),
+           "evaluations": ev.count, "search_s": search_s}
+    if best is None:
+        return out
+    evb = Evaluator(ev32.robot, ev32.scene, w.params, n, best)
+    pb = time_steps(evb, q, n, args.steps, args.warmup, flush, torch)
+    out.update({"table": str(best), "bits_searched_tensors": sum(getattr(best, k).bits for k in tensors),
+                "validation_error": e.error,
+                "configs_per_s": n * args.steps / (sum(pb["step"]) / 1000.0),
+                "speedup_vs_fp32": sum(per32["step"]) / sum(pb["step"]),
+                "stage_ms": {k: statistics.mean(pb[k]) for k in ("fk", "collision", "backward") if pb[k]}})
+    return out
+
+
+def fused_leg(w, q, n, vtable, args, flush, torch):
+    """FK, collision and backward fused per tile in one persistent launch
+    (the multi-problem kernel on this single problem): P and G never leave
+    the per-block scratch slices, which stay in L2."""
+    from paper_2310_07854_gb300.batched import BatchedEvaluator
+    out = {}
+    for name, table in (("fp32", F.FP32_TABLE), ("vapr", vtable)):
+        be = BatchedEvaluator([w], table=table, tile=128)
+        ms = time_graph(be.eval, args.steps, args.warmup, flush, torch)
+        out[name] = {"configs_per_s": n / (ms / 1000.0), "ms": ms, "tile": 128,
+                     "status": be.device_status()}
+        del be
+    return out
 
 
 def time_graph(fn, steps, warmup, flush_buf, torch):
@@ -372,16 +433,27 @@ def main():
     err = {k: float((a[k] - b[k]).abs().max()) for k in a}
     err_scale = {k: float(a[k].abs().max()) for k in a}
 
-    # roofline of the dominant kernel (FP32 table)
+    # roofline of the dominant kernel (FP32 table).  FK and backward are
+    # HBM-bound stages; the collision stage is bound by FP32 ALU work (every
+    # sphere/cuboid and self pair needs at least its bounding test).
     bpc = ev32.bytes_per_config()
     avg = {k: statistics.mean(v) for k, v in per32.items() if k != "step"}
     dom = max(avg, key=avg.get)
-    ach = bpc[dom] * n / (avg[dom] / 1000.0) / 1e9
     traffic = kernel_traffic(dom, "fp32")
-    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_source": peak_kind,
-            "traffic": None if traffic is None else traffic * n,
-            "algorithmic_bytes_per_launch": bpc[dom] * n}
+    if dom == "collision":
+        fpc = collision_flops_per_config(w)
+        ach = fpc * n / (avg[dom] / 1000.0) / 1e12
+        peak_alu = fp32_peak_tflops(peaks)
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
+                "frac": ach / peak_alu, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
+                "traffic": None if traffic is None else traffic * n,
+                "algorithmic_flops_per_launch": fpc * n, "algorithmic_bytes_per_launch": bpc[dom] * n}
+    else:
+        ach = bpc[dom] * n / (avg[dom] / 1000.0) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_source": peak_kind,
+                "traffic": None if traffic is None else traffic * n,
+                "algorithmic_bytes_per_launch": bpc[dom] * n}
     stages = {}
     for ev_, per_, name in ((ev32, per32, "fp32"), (evv, perv, "vapr")):
         bp = ev_.bytes_per_config()
@@ -424,6 +496,12 @@ def main():
                 dram[name][k] = {"ms": ms, "hbm_frac": bp[k] * nb / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]}
         del ebig, ebv, qb
 
+    fused = fused_leg(w, q, n, vtable, args, flush, torch)
+
+    found = None
+    if not args.no_search:
+        found = search_leg(w, ev32, q, n, args, flush, torch, per32)
+
     sur = None
     if not args.no_surrogate:
         sur = surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind)
@@ -448,6 +526,8 @@ def main():
                      "speedup_vs_fp32": value_v / value, "ms_per_step": tv / args.steps,
                      "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale},
             "stages": stages,
+            "fused_single_launch": fused,
+            "vapr_search": found,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,

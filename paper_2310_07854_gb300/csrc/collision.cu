@@ -6,26 +6,22 @@
 //
 // One warp per configuration (collision_config in stages.cuh); a block runs
 // COLL_WARPS of them at a time over tables staged once in shared memory.
-// Most sphere/cuboid pairs are far apart, so the exact distance is only
-// evaluated where a conservative test cannot rule the pair out.  Cuboids
-// are taken 64 at a time (lane l holds cuboids l and l + 32):
-//   1. each link's bounding sphere (centred on the link's middle sphere,
-//      radius over the actual positions) is tested against every cuboid's
-//      bounding sphere; each test's ballot writes the link's candidate list;
-//   2. every (sphere of the link, candidate) pair is enumerated densely over
-//      the lanes and tested sphere-against-bounding-sphere;
-//   3. survivors are compacted into a warp queue (ballot + popc) and the exact
-//      distance runs 32 pairs at a time, branch-free, one pair per lane.
-// A skipped pair provably has zero penetration (d_o(c) >= |c - t_o| - |h_o|);
-// SLACK metres cover the float32 rounding of the tests.
+// The environment term is sphere-major: each lane owns up to two spheres and
+// walks the cuboids in order, accumulating penetration and gradient in
+// registers.  Most sphere/cuboid pairs are far apart, so a sphere runs the
+// exact distance for cuboid o only when its centre lies within o's bounding
+// sphere grown by r + eta (a skipped pair provably has zero penetration,
+// since d_o(c) >= |c - t_o| - |h_o|; SLACK metres cover float32 rounding),
+// and the warp skips cuboid o outright when none of its spheres does.
+// (Measured on the 40-cuboid particle workload, this plain scheme issues
+// fewer instructions than per-link candidate lists or a compacted queue of
+// surviving pairs: the bounding test is cheaper than the bookkeeping.)
 //
-// Determinism: queue entries of one sphere are contiguous and in ascending
-// cuboid order, and they are added to the sphere's accumulator one per
-// round (lanes of rank r in round r).  Every sphere therefore sums its
-// contributions sequentially in cuboid order, independent of where queue
-// flushes fall or which zero-penetration pairs survive the culling, so the
-// result of a configuration does not depend on the batch it is in.  Active
-// self pairs are applied one lane at a time in pair order.
+// Determinism: every sphere adds its terms in cuboid order in one register,
+// and a skipped pair would have added exactly zero, so the result of a
+// configuration does not depend on the batch it is in or on which pairs the
+// bounding test lets through.  Active self pairs are applied one lane at a
+// time in pair order.
 #include "stages.cuh"
 
 namespace vapr {

@@ -136,8 +136,6 @@ __device__ __forceinline__ void fk_store_xform(int J, const float4* T, uint32_t*
 }
 
 // ------------------------------------------------------- collision (warp)
-constexpr int QCAP = 64;         // warp queue of (sphere, cuboid) pairs
-constexpr int CHUNK = 64;        // cuboids per culling pass
 constexpr float SLACK = 1e-4f;   // metres: covers float32 rounding of the culls
 
 struct SceneSm {
@@ -176,23 +174,14 @@ __device__ inline void load_scene(const RobotArgs& r, const SceneArgs& sc, float
 
 // One warp's working set for one configuration.
 struct CollWarp {
-  float4* P;        // [S] (x, y, z, r)
-  float4* acc;      // [S] (D, gx, gy, gz)
-  float4* lb;       // [J] link bounding sphere (centre, radius)
-  uint32_t* queue;  // [QCAP] sphere | cuboid << 16
-  int* ccount;      // [J]
-  uint16_t* cand;   // [J][CHUNK] candidate cuboids of each link
-  uint32_t* far;    // [MAX_SPHERES / 32] spheres cleared by a broad-phase estimate
+  float4* P;    // [S] (x, y, z, r)
+  float4* acc;  // [S] (D, gx, gy, gz)
 };
 
 __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp& w) {
+  (void)J;
   w.P = b.take<float4>(S);
   w.acc = b.take<float4>(S);
-  w.lb = b.take<float4>(J);
-  w.queue = b.take<uint32_t>(QCAP);
-  w.ccount = b.take<int>(J);
-  w.cand = b.take<uint16_t>((size_t)J * CHUNK);
-  w.far = b.take<uint32_t>(VAPR_MAX_SPHERES / 32);
 }
 
 // Radii into P[].w and zero accumulators (once per robot).
@@ -203,61 +192,37 @@ __device__ __forceinline__ void init_coll_warp(const RobotArgs& r, const CollWar
   }
 }
 
-// Exact narrow phase of queue entries 0..cnt-1 (one per lane) and their
-// accumulation, rank by rank, into acc: entries of a sphere are contiguous
-// and in cuboid order, so each sphere sums its contributions sequentially.
-__device__ __forceinline__ void coll_flush(const SceneSm& m, const CollWarp& w, int cnt, float eta,
-                                           float w_c, int lane) {
-  const bool have = lane < cnt;
-  const uint32_t e = have ? w.queue[lane] : 0xffffffffu;
-  const int s = (int)(e & 0xffffu), o = (int)(e >> 16);
-  float dD = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-  if (have) {
-    const float4 c = w.P[s];
-    const float4 A0 = m.cubA[3 * o], A1 = m.cubA[3 * o + 1], A2 = m.cubA[3 * o + 2];
-    const float4 H = m.cubH[o];
-    const float dx = c.x - A0.w, dy = c.y - A1.w, dz = c.z - A2.w;
-    const float x0 = fmaf(A0.x, dx, fmaf(A0.y, dy, A0.z * dz));
-    const float x1 = fmaf(A1.x, dx, fmaf(A1.y, dy, A1.z * dz));
-    const float x2 = fmaf(A2.x, dx, fmaf(A2.y, dy, A2.z * dz));
-    const float u0 = fabsf(x0) - H.x, u1 = fabsf(x1) - H.y, u2 = fabsf(x2) - H.z;
-    const float v0 = fmaxf(u0, 0.f), v1 = fmaxf(u1, 0.f), v2 = fmaxf(u2, 0.f);
-    const float n2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-    const bool outside = u0 > 0.f || u1 > 0.f || u2 > 0.f;
-    // inside: the face of the largest u (lowest axis on ties)
-    const int k = (u0 >= u1 && u0 >= u2) ? 0 : (u1 >= u2 ? 1 : 2);
-    const float umax = fmaxf(u0, fmaxf(u1, u2));
-    const float rs = n2 > 0.f ? rsqrtf(n2) : 0.f;  // 1/|max(u,0)|
-    const float d = outside ? n2 * rs : umax;
-    const float pen = c.w + eta - d;
-    if (pen > 0.f) {
-      const float inv = outside ? rs : 0.f;
-      const float s0 = x0 >= 0.f ? 1.f : -1.f, s1 = x1 >= 0.f ? 1.f : -1.f,
-                  s2 = x2 >= 0.f ? 1.f : -1.f;
-      const float l0 = outside ? s0 * v0 * inv : (k == 0 ? s0 : 0.f);
-      const float l1 = outside ? s1 * v1 * inv : (k == 1 ? s1 : 0.f);
-      const float l2 = outside ? s2 * v2 * inv : (k == 2 ? s2 : 0.f);
-      dD = pen;  // gradient of the hinge: -grad d, scaled by w_coll
-      gx = -w_c * fmaf(A0.x, l0, fmaf(A1.x, l1, A2.x * l2));
-      gy = -w_c * fmaf(A0.y, l0, fmaf(A1.y, l1, A2.y * l2));
-      gz = -w_c * fmaf(A0.z, l0, fmaf(A1.z, l1, A2.z * l2));
-    }
-  }
-  const int prev = __shfl_up_sync(FULL_MASK, s, 1);
-  const bool head = lane == 0 || !have || s != prev;
-  const unsigned heads = __ballot_sync(FULL_MASK, head);
-  const int rank = lane - (31 - __clz(heads & (FULL_MASK >> (31 - lane))));
-  const int rounds = __reduce_max_sync(FULL_MASK, have ? rank : 0);
-  for (int r = 0; r <= rounds; ++r) {
-    if (have && rank == r) {
-      float4 a = w.acc[s];
-      a.x += dD;
-      a.y += gx;
-      a.z += gy;
-      a.w += gz;
-      w.acc[s] = a;
-    }
-    __syncwarp();
+// Exact sphere-cuboid term: penetration max(0, r + eta - d) of the sphere
+// (c, c.w = r) against cuboid o, and its gradient -w_c grad d, added to acc
+// (x: D, yzw: G).  Zero when the sphere is clear of the cuboid.
+__device__ __forceinline__ void box_term(const SceneSm& m, int o, const float4& c, float eta, float w_c,
+                                         float4& acc) {
+  const float4 A0 = m.cubA[3 * o], A1 = m.cubA[3 * o + 1], A2 = m.cubA[3 * o + 2];
+  const float4 H = m.cubH[o];
+  const float dx = c.x - A0.w, dy = c.y - A1.w, dz = c.z - A2.w;
+  const float x0 = fmaf(A0.x, dx, fmaf(A0.y, dy, A0.z * dz));
+  const float x1 = fmaf(A1.x, dx, fmaf(A1.y, dy, A1.z * dz));
+  const float x2 = fmaf(A2.x, dx, fmaf(A2.y, dy, A2.z * dz));
+  const float u0 = fabsf(x0) - H.x, u1 = fabsf(x1) - H.y, u2 = fabsf(x2) - H.z;
+  const float v0 = fmaxf(u0, 0.f), v1 = fmaxf(u1, 0.f), v2 = fmaxf(u2, 0.f);
+  const float n2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+  const bool outside = u0 > 0.f || u1 > 0.f || u2 > 0.f;
+  // inside: the face of the largest u (lowest axis on ties)
+  const int k = (u0 >= u1 && u0 >= u2) ? 0 : (u1 >= u2 ? 1 : 2);
+  const float umax = fmaxf(u0, fmaxf(u1, u2));
+  const float rs = n2 > 0.f ? rsqrtf(n2) : 0.f;  // 1/|max(u,0)|
+  const float d = outside ? n2 * rs : umax;
+  const float pen = c.w + eta - d;
+  if (pen > 0.f) {
+    const float inv = outside ? rs : 0.f;
+    const float s0 = x0 >= 0.f ? 1.f : -1.f, s1 = x1 >= 0.f ? 1.f : -1.f, s2 = x2 >= 0.f ? 1.f : -1.f;
+    const float l0 = outside ? s0 * v0 * inv : (k == 0 ? s0 : 0.f);
+    const float l1 = outside ? s1 * v1 * inv : (k == 1 ? s1 : 0.f);
+    const float l2 = outside ? s2 * v2 * inv : (k == 2 ? s2 : 0.f);
+    acc.x += pen;  // gradient of the hinge: -grad d, scaled by w_coll
+    acc.y += -w_c * fmaf(A0.x, l0, fmaf(A1.x, l1, A2.x * l2));
+    acc.z += -w_c * fmaf(A0.y, l0, fmaf(A1.y, l1, A2.y * l2));
+    acc.w += -w_c * fmaf(A0.z, l0, fmaf(A1.z, l1, A2.z * l2));
   }
 }
 
@@ -270,12 +235,12 @@ struct CollOut {
 };
 
 // The whole collision stage of one configuration by one warp: P row in,
-// cost, D and G rows out.  Culling is conservative (see collision.cu).
+// cost, D and G rows out (see collision.cu for the scheme).
 // COHERENT reads the P row with loads that see writes made earlier in the
 // same kernel (the fused multi-problem kernel); otherwise through the
 // read-only cache.  MASKED takes a per-sphere distance estimate `est` (this
 // configuration's row): spheres with est - r >= margin skip the cuboid
-// tests, and only the others shape the link bounding spheres.
+// tests.
 template <bool COHERENT = false, bool MASKED = false>
 __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, const RobotSm& rb,
                                                  const SceneSm& m, const CollWarp& w,
@@ -284,8 +249,8 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
                                                  float w_c, float w_s, const CollOut& out,
                                                  int lane, const float* est = nullptr,
                                                  float margin = 0.f) {
-  const int J = r.J, S = r.S, NP = r.NP;
-  const unsigned lt_mask = (1u << lane) - 1u;
+  (void)rb;
+  const int S = r.S, NP = r.NP;
   // ---- 1. sphere centres (one word per lane)
   {
     const int nv = 3 * S;
@@ -303,102 +268,38 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
     });
   }
   __syncwarp();
-  if constexpr (MASKED) {
-    for (int s0 = 0; s0 < S; s0 += 32) {
-      const int s = s0 + lane;
-      const bool clear = s < S && __ldg(est + s) - w.P[s].w >= margin;
-      const unsigned bal = __ballot_sync(FULL_MASK, clear);
-      if (lane == 0) w.far[s0 >> 5] = bal;
+  // ---- 2. environment, sphere-major: lane owns spheres base + lane and
+  //      base + 32 + lane and sums their terms in registers, cuboid by
+  //      cuboid in order.  A sphere takes cuboid o's exact test only when it
+  //      lies within the cuboid's bounding sphere grown by r + eta (+ SLACK);
+  //      the warp skips o when none of its spheres does.
+  for (int base = 0; base < S; base += 64) {
+    const int sa = base + lane, sb = base + 32 + lane;
+    bool va = sa < S, vb = sb < S;
+    const float4 pa = va ? w.P[sa] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 pb = vb ? w.P[sb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (MASKED) {
+      va = va && __ldg(est + sa) - pa.w < margin;
+      vb = vb && __ldg(est + sb) - pb.w < margin;
     }
-    __syncwarp();
-  }
-  // ---- 2. link bounding spheres centred on the middle sphere of the link;
-  //      radius = max |c_s - centre| + r_s (integer atomicMax on float bits)
-  if (lane < J) {
-    const int b = rb.start[lane], e = rb.start[lane + 1];
-    const float4 ctr = e > b ? w.P[rb.order[b + (e - b) / 2]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    w.lb[lane] = make_float4(ctr.x, ctr.y, ctr.z, (e > b && !MASKED) ? 0.f : -1.f);
-  }
-  __syncwarp();
-  for (int s = lane; s < S; s += 32) {
-    if constexpr (MASKED)
-      if ((w.far[s >> 5] >> (s & 31)) & 1u) continue;
-    const float4 p = w.P[s];
-    const float4 b = w.lb[rb.link0[s]];
-    const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
-    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rad = (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f) + p.w + SLACK;
-    atomicMax(reinterpret_cast<int*>(w.lb + rb.link0[s]) + 3, __float_as_int(rad));
-  }
-  __syncwarp();
-  // ---- 3. environment: cull, compact, evaluate (CHUNK cuboids per pass)
-  for (int base = 0; base < O; base += CHUNK) {
-    const int o0 = base + lane, o1 = base + 32 + lane;
-    const float4 C0 = o0 < O ? m.cubC[o0] : make_float4(0.f, 0.f, 0.f, -1e30f);
-    const float4 C1 = o1 < O ? m.cubC[o1] : make_float4(0.f, 0.f, 0.f, -1e30f);
-    for (int L = 0; L < J; ++L) {
-      const float4 b = w.lb[L];
-      bool n0 = false, n1 = false;
-      if (b.w >= 0.f) {
-        const float ax = b.x - C0.x, ay = b.y - C0.y, az = b.z - C0.z;
-        const float t0 = b.w + C0.w;
-        n0 = C0.w > 0.f && fmaf(ax, ax, fmaf(ay, ay, az * az)) < t0 * t0;
-        const float bx = b.x - C1.x, by = b.y - C1.y, bz = b.z - C1.z;
-        const float t1 = b.w + C1.w;
-        n1 = C1.w > 0.f && fmaf(bx, bx, fmaf(by, by, bz * bz)) < t1 * t1;
-      }
-      const unsigned m0 = __ballot_sync(FULL_MASK, n0), m1 = __ballot_sync(FULL_MASK, n1);
-      uint16_t* cl = w.cand + L * CHUNK;
-      if (n0) cl[__popc(m0 & lt_mask)] = (uint16_t)o0;
-      if (n1) cl[__popc(m0) + __popc(m1 & lt_mask)] = (uint16_t)o1;
-      if (lane == 0) w.ccount[L] = __popc(m0) + __popc(m1);
-    }
-    __syncwarp();
-    int qn = 0;
-    for (int L = 0; L < J; ++L) {  // (sphere of L, candidate): sphere-major, dense over lanes
-      const int cl_n = w.ccount[L];
-      const int s0 = rb.start[L], ns = rb.start[L + 1] - s0;
-      const int total = cl_n * ns;
-      if (total == 0) continue;
-      const float rcp = 1.0f / (float)cl_n;
-      const uint16_t* cl = w.cand + L * CHUNK;
-      for (int t = 0; t < total; t += 32) {
-        const int idx = t + lane;
-        bool nr = false;
-        int s = 0, o = 0;
-        if (idx < total) {
-          int js = __float2int_rd(((float)idx + 0.5f) * rcp);  // idx / cl_n
-          int jc = idx - js * cl_n;
-          if (jc >= cl_n) { ++js; jc -= cl_n; }  // exact quotient whatever the rounding
-          if (jc < 0) { --js; jc += cl_n; }
-          s = rb.order[s0 + js];
-          o = cl[jc];
-          const float4 p = w.P[s];
-          const float4 C = m.cubC[o];
-          const float dx = p.x - C.x, dy = p.y - C.y, dz = p.z - C.z;
-          const float thr = p.w + C.w;
-          nr = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < thr * thr;
-          if constexpr (MASKED) nr = nr && !((w.far[s >> 5] >> (s & 31)) & 1u);
-        }
-        const unsigned bal = __ballot_sync(FULL_MASK, nr);
-        if (nr) w.queue[qn + __popc(bal & lt_mask)] = (uint32_t)s | ((uint32_t)o << 16);
-        qn += __popc(bal);
-        if (qn >= 32) {
-          __syncwarp();
-          coll_flush(m, w, 32, eta, w_c, lane);
-          const int rest = qn - 32;
-          const uint32_t moved = lane < rest ? w.queue[32 + lane] : 0u;
-          __syncwarp();
-          if (lane < rest) w.queue[lane] = moved;
-          qn = rest;
-          __syncwarp();
+    float4 acca = make_float4(0.f, 0.f, 0.f, 0.f), accb = acca;
+    if (__any_sync(FULL_MASK, va || vb)) {
+      for (int o = 0; o < O; ++o) {
+        const float4 C = m.cubC[o];
+        const float ax = pa.x - C.x, ay = pa.y - C.y, az = pa.z - C.z, ta = pa.w + C.w;
+        const float bx = pb.x - C.x, by = pb.y - C.y, bz = pb.z - C.z, tb = pb.w + C.w;
+        const bool na = va && fmaf(ax, ax, fmaf(ay, ay, az * az)) < ta * ta;
+        const bool nb = vb && fmaf(bx, bx, fmaf(by, by, bz * bz)) < tb * tb;
+        if (__any_sync(FULL_MASK, na || nb)) {
+          if (na) box_term(m, o, pa, eta, w_c, acca);
+          if (nb) box_term(m, o, pb, eta, w_c, accb);
         }
       }
     }
-    __syncwarp();
-    if (qn > 0) coll_flush(m, w, qn, eta, w_c, lane);  // runs never span passes
-    __syncwarp();
+    if (sa < S) w.acc[sa] = acca;
+    if (sb < S) w.acc[sb] = accb;
   }
+  __syncwarp();
   // ---- 4. self-collision over the pair list
   float selfsum = 0.f;
   for (int pb = 0; pb < NP; pb += 32) {
