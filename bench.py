@@ -54,6 +54,9 @@ def parse_args():
                     help="skip the learned-surrogate leg (training + gated collision)")
     ap.add_argument("--surrogate-epochs", type=int, default=80)
     ap.add_argument("--no-search", action="store_true", help="skip the VaPr format search leg")
+    ap.add_argument("--kernel", choices=["fk", "collision", "backward", "mlp_infer", "step"], default=None,
+                    help="profiling mode: run only this stage (--warmup launches, then --steps timed) on "
+                         "--configs configurations of the workload and print its CUDA-event time")
     ap.add_argument("--search-samples", type=int, default=300)
     ap.add_argument("--configs", type=int, default=0,
                     help="override the batch size (configurations per GPU)")
@@ -197,19 +200,33 @@ def time_steps(ev, q, n, steps, warmup, flush_buf, torch):
     return per
 
 
-def kernel_traffic(stage: str, table: str):
-    """DRAM bytes per configuration from a committed ncu summary, if one
-    exists for the current kernel source (else None)."""
+KERNEL_SOURCES = {
+    "fk": ("fk.cu", "stages.cuh", "exmy.cuh", "common.cuh"),
+    "collision": ("collision.cu", "stages.cuh", "exmy.cuh", "common.cuh"),
+    "backward": ("backward.cu", "stages.cuh", "exmy.cuh", "common.cuh"),
+}
+
+
+def kernel_source_sha(stage: str) -> str:
+    """Hash of every source file the stage's kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[stage]:
+        h.update(open(os.path.join(ROOT, "paper_2310_07854_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(stage: str, table: str, n: int):
+    """DRAM bytes per configuration of one launch on n configurations, from
+    a committed ncu capture of the current kernel source at that size (else
+    None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             data = json.load(f)
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2310_07854_gb300", "csrc", {"fk": "fk.cu", "collision": "collision.cu",
-                                                                  "backward": "backward.cu"}[stage])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    ent = data.get(f"{stage}:{table}")
+    h = kernel_source_sha(stage)
+    ent = data.get(f"{stage}:{table}:{n}")
     if not ent or ent.get("source_sha") != h:
         return None
     return ent.get("dram_bytes_per_config")
@@ -367,10 +384,48 @@ def surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind):
     }
 
 
+def kernel_mode(args):
+    """One stage alone, for ncu captures: a fixed number of launches of one
+    kernel on a chosen size, no flush, no other legs."""
+    import torch
+    from paper_2310_07854_gb300 import binding as B
+    from paper_2310_07854_gb300.path import Evaluator
+    w = synth.make_workload(args.workload)
+    n = args.configs or w.n
+    q = torch.as_tensor(synth.make_q(500, n), device="cuda")
+    table = F.FormatTable.parse(args.table) if args.table != "fp32" else F.FP32_TABLE
+    if args.kernel == "mlp_infer":
+        st = B.alloc_mlp_state()
+        B.vapr_mlp_init(st, torch.as_tensor(synth.init_mlp_params(5), device="cuda"))
+        u = torch.as_tensor(synth.uniform_points(3, [-1, -1, -1], [1, 1, 1], n), device="cuda")
+        out = torch.empty(n, device="cuda")
+        fn = lambda: B.vapr_mlp_forward(st, u, n, out)
+    else:
+        ev = Evaluator(w.robot, w.scene, w.params, n, table)
+        ev.fk(q, n)
+        ev.collision(n)
+        fn = {"fk": lambda: ev.fk(q, n), "collision": lambda: ev.collision(n),
+              "backward": lambda: ev.backward(q, n), "step": lambda: ev.step(q, n)}[args.kernel]
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "units": n, "table": str(table),
+                      "ms_per_launch": ms, "device_error": B.vapr_device_error()}))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel:
+        return kernel_mode(args)
     world, rank, local = replicas.dist_env()
     import torch
     if not torch.cuda.is_available():
@@ -439,7 +494,7 @@ def main():
     bpc = ev32.bytes_per_config()
     avg = {k: statistics.mean(v) for k, v in per32.items() if k != "step"}
     dom = max(avg, key=avg.get)
-    traffic = kernel_traffic(dom, "fp32")
+    traffic = kernel_traffic(dom, "fp32", n)
     if dom == "collision":
         fpc = collision_flops_per_config(w)
         ach = fpc * n / (avg[dom] / 1000.0) / 1e12
