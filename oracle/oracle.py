@@ -74,6 +74,7 @@ def _load():
             "or_mlp_forward": (None, [P, i32, P, i64, P]),
             "or_mlp_forward_bf16act": (None, [P, i32, P, i64, P]),
             "or_mlp_grads": (dbl, [P, i32, P, P, i64, dbl, P]),
+            "or_swept": (None, [i32, P, i32, P, P, dbl, dbl, P, i64, i32, i32, P, P, P, P, dbl]),
             "or_num_threads": (i32, []),
         }
         for name, (res, args) in sig.items():
@@ -224,6 +225,21 @@ def collision(robot, scene, params, pos, kink_eps: float = 1e-4):
                          params.eta, params.eta_self, params.w_coll,
                          params.w_self, _p(pos), n, _p(cost), _p(dist),
                          _p(grad), _p(kink), kink_eps)
+    return {"cost": cost, "dist": dist, "grad": grad, "kink": kink.astype(bool)}
+
+
+def swept(robot, scene, params, pos, horizon: int, samples: int, kink_eps: float = 1e-4):
+    """Swept-sphere environment cost -> dict(cost [n], dist [n, S], grad [n, S, 3], kink [n, S])."""
+    pos = _c(pos, np.float64)
+    n, ns = pos.shape[0], pos.shape[1]
+    cost = np.empty(n, np.float64)
+    dist = np.empty((n, ns), np.float64)
+    grad = np.empty((n, ns, 3), np.float64)
+    kink = np.empty((n, ns), np.int32)
+    _load().or_swept(ns, _p(_c(robot.sphere_local, np.float32)), scene.pose.shape[0],
+                     _p(_c(scene.pose, np.float32)), _p(_c(scene.half_ext, np.float32)),
+                     float(params.eta), float(params.w_coll), _p(pos), n, horizon, samples,
+                     _p(cost), _p(dist), _p(grad), _p(kink), float(kink_eps))
     return {"cost": cost, "dist": dist, "grad": grad, "kink": kink.astype(bool)}
 
 

@@ -394,6 +394,67 @@ void or_collision(int ns, const float* sphere_local, int npairs,
 /* Backward kinematics: dc_s/dq_j = a_j x (c_s - o_j) for every sphere on a
  * link at or beyond joint j (a revolute joint turns everything after it),
  * so dC/dq_j = sum_s G_s . (a_j x (c_s - o_j)). */
+/* Hinge sum over the cuboids at point x for a sphere of radius r: returns
+ * sum_o max(0, r + eta - d_o(x)) and adds -grad of it to g; sets *kink when
+ * x is within kink_eps of a hinge activation or, where active, of an
+ * inside-argmax tie. */
+static double hinge_sum(int no, const float* pose, const float* half, double r, double eta,
+                        const double x[3], double g[3], int* kink, double kink_eps) {
+  double D = 0.0;
+  for (int o = 0; o < no; ++o) {
+    double gd[3], margin;
+    const double d = box_sdf(pose + 12 * o, half + 3 * o, x, gd, &margin);
+    const double pen = r + eta - d;
+    if (fabs(pen) < kink_eps) *kink = 1;
+    if (pen > 0.0) {
+      D += pen;
+      for (int k = 0; k < 3; ++k) g[k] -= gd[k];
+      if (margin < kink_eps) *kink = 1;
+    }
+  }
+  return D;
+}
+
+void or_swept(int ns, const float* sphere_local, int no, const float* pose, const float* half,
+              double eta, double w_c, const double* pos, int64_t n, int horizon, int samples,
+              double* cost, double* dist, double* grad, int32_t* kink, double kink_eps) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t c = 0; c < n; ++c) {
+    const int h = (int)(c % horizon);
+    const int64_t nxt = h + 1 < horizon ? c + 1 : c;  /* the row this one sweeps toward */
+    const double* P = pos + (int64_t)ns * 3 * c;
+    const double* Pn = pos + (int64_t)ns * 3 * nxt;
+    const double* Pp = h > 0 ? pos + (int64_t)ns * 3 * (c - 1) : NULL;  /* sweeps toward c */
+    double total = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      const double r = sphere_local[4 * s + 3];
+      double Ds = 0.0, gs[3] = {0.0, 0.0, 0.0};
+      int flag = 0;
+      for (int k = 0; k < samples; ++k) {
+        const double a = (double)k / (double)samples;
+        double x[3], g[3] = {0.0, 0.0, 0.0};
+        /* own points: weight (1 - a), plus a when the row sweeps toward itself */
+        for (int i = 0; i < 3; ++i) x[i] = (1.0 - a) * P[3 * s + i] + a * Pn[3 * s + i];
+        Ds += hinge_sum(no, pose, half, r, eta, x, g, &flag, kink_eps);
+        const double wown = nxt == c ? 1.0 : 1.0 - a;
+        for (int i = 0; i < 3; ++i) gs[i] += wown * g[i];
+        /* the previous row's points depend on this row with weight a */
+        if (Pp && a > 0.0) {
+          double gp[3] = {0.0, 0.0, 0.0};
+          for (int i = 0; i < 3; ++i) x[i] = (1.0 - a) * Pp[3 * s + i] + a * P[3 * s + i];
+          hinge_sum(no, pose, half, r, eta, x, gp, &flag, kink_eps);
+          for (int i = 0; i < 3; ++i) gs[i] += a * gp[i];
+        }
+      }
+      dist[(int64_t)ns * c + s] = Ds;
+      for (int i = 0; i < 3; ++i) grad[(int64_t)ns * 3 * c + 3 * s + i] = w_c * gs[i];
+      total += w_c * Ds;
+      if (kink) kink[(int64_t)ns * c + s] = flag;
+    }
+    cost[c] = total;
+  }
+}
+
 void or_backward(int nj, const float* joint_fixed, int ns,
                  const float* sphere_local, const int32_t* sphere_link,
                  const float* q, const double* grad, const double* dcost,

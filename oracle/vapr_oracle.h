@@ -97,6 +97,20 @@ void or_backward(int nj, const float* joint_fixed, int ns,
                  const float* q, const double* grad, const double* dcost,
                  int64_t n, double* jgrad);
 
+/* ---- swept-sphere environment cost (closest_pt_swept, Sec. III-C) ------- */
+/* Rows are trajectories of `horizon` consecutive configurations.  The sphere
+ * s of row h is swept toward row h+1: K points p_k = (1 - a_k) c_h + a_k c_h'
+ * with a_k = k / K (k = 0..K-1) and h' = h+1, or h' = h on a trajectory's
+ * last row.  D_s = sum_k sum_o max(0, r_s + eta - d_o(p_k)),
+ * cost = w_c sum_s D_s, and grad = d(total swept cost)/dc_h: (1 - a_k) times
+ * the hinge gradient at the row's own points plus a_k times it at the
+ * previous row's points (and at its own points on a last row, where h' = h).
+ * kink [n][ns] (may be NULL) flags spheres with a point within kink_eps of a
+ * gradient discontinuity.  pos [n][ns][3]; n a multiple of horizon. */
+void or_swept(int ns, const float* sphere_local, int no, const float* pose, const float* half,
+              double eta, double w_c, const double* pos, int64_t n, int horizon, int samples,
+              double* cost, double* dist, double* grad, int32_t* kink, double kink_eps);
+
 /* ---- scene signed distance (surrogate labels) ----------------------------- */
 /* sdf(p) = min_o d_o(p) */
 void or_scene_sdf(int no, const float* pose, const float* half,
