@@ -276,6 +276,24 @@ def search_leg(w, ev32, q, n, args, flush, torch, per32):
     return out
 
 
+def swept_leg(w, ev32, n, args, flush, torch, samples=4):
+    """Swept-sphere environment cost (closest_pt_swept) on the workload's
+    trajectories (K points per row), FP32 and the VaPr table's D/G formats."""
+    from paper_2310_07854_gb300 import binding as B
+    S = w.robot.n_spheres
+    out = {"samples": samples, "horizon": w.horizon}
+    for name, table in (("fp32", F.FP32_TABLE), ("vapr", F.FormatTable.parse(args.table))):
+        t = F.FormatTable(pos=F.FP32, dist=table.dist, grad=table.grad)
+        cost = torch.empty(n, device="cuda")
+        dist = B.alloc_packed(n, S, t.dist)
+        grad = B.alloc_packed(n, 3 * S, t.grad)
+        fn = lambda: B.vapr_swept_cost(ev32.robot, ev32.scene, w.params, ev32.pos, n, w.horizon, samples,
+                                       t, cost, dist, grad)
+        ms = time_graph(fn, args.steps, args.warmup, flush, torch)
+        out[name] = {"table": str(t), "ms": ms, "configs_per_s": n / (ms / 1000.0)}
+    return out
+
+
 def fused_leg(w, q, n, vtable, args, flush, torch):
     """FK, collision and backward fused per tile in one persistent launch
     (the multi-problem kernel on this single problem): P and G never leave
@@ -552,6 +570,8 @@ def main():
         del ebig, ebv, qb
 
     fused = fused_leg(w, q, n, vtable, args, flush, torch)
+    ev32.fk(q, n)
+    swept = swept_leg(w, ev32, n, args, flush, torch)
 
     found = None
     if not args.no_search:
@@ -582,6 +602,7 @@ def main():
                      "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale},
             "stages": stages,
             "fused_single_launch": fused,
+            "swept": swept,
             "vapr_search": found,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,

@@ -192,6 +192,29 @@ vapr_status vapr_backward(const vapr_robot* robot, const float* q,
                           const vapr_format_table* table, void* jgrad_packed,
                           void* stream);
 
+/* ---- swept-sphere environment cost (trajectory optimisation) -------------- */
+#define VAPR_MAX_SWEPT_SAMPLES 64
+
+/* The environment cost of spheres swept between consecutive timesteps, whose
+ * gradient is closest_pt_swept (Sec. III-C names the tensor; the paper
+ * prints no formula, this is the library's reading).  The n rows of
+ * pos_packed are trajectories of `horizon` consecutive configurations.  Row
+ * h sweeps each sphere toward row h' = h+1 (h' = h on a trajectory's last
+ * row) at K = samples points p_k = c_h + (k/K)(c_h' - c_h), k = 0..K-1:
+ *   D_s = sum_k sum_o max(0, r_s + eta - d_o(p_k)),  cost = w_coll sum_s D_s,
+ *   G_s = d(total swept cost of the trajectory)/dc_s of this row: the row's
+ *   own points weighted 1 - k/K (1 on a last row) plus the previous row's
+ *   points weighted k/K.
+ * Self-collision is not part of it (vapr_collision_cost has it).  With
+ * samples = 1 the results equal vapr_collision_cost's environment term
+ * bit for bit.  Formats: P in table->pos, D in table->dist, G in
+ * table->grad.  n % horizon == 0, 1 <= samples <= VAPR_MAX_SWEPT_SAMPLES.
+ * cost (float32 [n]), dist_packed and grad_packed may each be NULL. */
+vapr_status vapr_swept_cost(const vapr_robot* robot, const vapr_scene* scene,
+                            const vapr_cost_params* params, const void* pos_packed, int64_t n,
+                            int32_t horizon, int32_t samples, const vapr_format_table* table,
+                            float* cost, void* dist_packed, void* grad_packed, void* stream);
+
 /* ---- tensor-core GEMM (building block of the learned surrogate) ----------- */
 /* C = A * B^T on the tcgen05 tensor cores (TMA-fed shared memory, FP32
  * accumulation in tensor memory).  A: bfloat16 [M][K], B: bfloat16 [N][K],

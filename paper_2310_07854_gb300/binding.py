@@ -134,6 +134,10 @@ SIGNATURES = {
                                               ctypes.POINTER(vapr_cost_params), _P, _i64,
                                               ctypes.POINTER(vapr_format_table), _P, _P, _P, _P,
                                               _P]),
+    "vapr_swept_cost": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
+                                       ctypes.POINTER(vapr_cost_params), _P, _i64, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.POINTER(vapr_format_table), _P, _P, _P,
+                                       _P]),
     "vapr_mlp_state_bytes": (ctypes.c_size_t, []),
     "vapr_mlp_init": (ctypes.c_int, [_P, _P, _P]),
     "vapr_mlp_get_params": (ctypes.c_int, [_P, _P, _P]),
@@ -319,6 +323,16 @@ def vapr_collision_cost(robot: DeviceRobot, scene: DeviceScene, params, pos_pack
                                        ctypes.byref(cp), _ptr(pos_packed), n, ctypes.byref(ct),
                                        _ptr(cost), _ptr(dist_packed), _ptr(grad_packed),
                                        _stream(stream)), "vapr_collision_cost")
+
+
+def vapr_swept_cost(robot: DeviceRobot, scene: DeviceScene, params, pos_packed, n, horizon, samples,
+                    table, cost=None, dist_packed=None, grad_packed=None, stream=None):
+    ct = to_c_table(table)
+    cp = params if isinstance(params, vapr_cost_params) else cost_params(params)
+    _check(_load().vapr_swept_cost(ctypes.byref(robot.c), ctypes.byref(scene.c), ctypes.byref(cp),
+                                   _ptr(pos_packed), n, horizon, samples, ctypes.byref(ct), _ptr(cost),
+                                   _ptr(dist_packed), _ptr(grad_packed), _stream(stream)),
+           "vapr_swept_cost")
 
 
 def vapr_backward(robot: DeviceRobot, q, xform_packed, grad_packed, dcost, n,

@@ -234,6 +234,60 @@ struct CollOut {
   int grad_words;
 };
 
+// Decodes the sphere centres of one packed P row into P[s].xyz (one word per
+// lane; .w is left alone).  COHERENT: loads that see writes made earlier in
+// the same kernel.
+template <bool COHERENT>
+__device__ __forceinline__ void load_centres(const uint32_t* prow, const DevFmt& fP, int S, float4* P,
+                                             int lane) {
+  const int nv = 3 * S;
+  dispatch_kind(fP.kind, [&](auto kc) {
+    constexpr int K = decltype(kc)::value;
+    const int kw = per_word<K>(fP);
+    const int nw = (nv + kw - 1) / kw;
+    for (int wd = lane; wd < nw; wd += 32) {
+      const uint32_t word = COHERENT ? __ldcg(prow + wd) : __ldg(prow + wd);
+      unpack_word_t<K>(word, wd, nv, fP, [&](int i, float x) {
+        const int s = i / 3;
+        reinterpret_cast<float*>(P + s)[i - 3 * s] = x;
+      });
+    }
+  });
+}
+
+// Cost (w_c sum_s acc[s].x + extra), the packed D (acc.x) and G (acc.yzw)
+// rows of one configuration, one word per lane; then zeroes acc.
+__device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const DevFmt& fD, const DevFmt& fG,
+                                             float w_c, float extra, const CollOut& out, int lane) {
+  float local = 0.f;
+  for (int s = lane; s < S; s += 32) local += w.acc[s].x;
+  local = w_c * local + extra;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULL_MASK, local, off);
+  if (out.cost && lane == 0) *out.cost = local;
+  if (out.dist) {
+    dispatch_kind(fD.kind, [&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      for (int wd = lane; wd < out.dist_words; wd += 32)
+        out.dist[wd] = pack_word_t<K>(wd, S, fD, [&](int i) { return w.acc[i].x; });
+    });
+  }
+  if (out.grad) {
+    const int nv = 3 * S;
+    dispatch_kind(fG.kind, [&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      for (int wd = lane; wd < out.grad_words; wd += 32)
+        out.grad[wd] = pack_word_t<K>(wd, nv, fG, [&](int i) {
+          const int s = i / 3;
+          return reinterpret_cast<const float*>(w.acc + s)[1 + i - 3 * s];
+        });
+    });
+  }
+  __syncwarp();
+  for (int s = lane; s < S; s += 32) w.acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncwarp();
+}
+
 // The whole collision stage of one configuration by one warp: P row in,
 // cost, D and G rows out (see collision.cu for the scheme).
 // COHERENT reads the P row with loads that see writes made earlier in the
@@ -252,21 +306,7 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
   (void)rb;
   const int S = r.S, NP = r.NP;
   // ---- 1. sphere centres (one word per lane)
-  {
-    const int nv = 3 * S;
-    dispatch_kind(fP.kind, [&](auto kc) {
-      constexpr int K = decltype(kc)::value;
-      const int kw = per_word<K>(fP);
-      const int nw = (nv + kw - 1) / kw;
-      for (int wd = lane; wd < nw; wd += 32) {
-        const uint32_t word = COHERENT ? __ldcg(prow + wd) : __ldg(prow + wd);
-        unpack_word_t<K>(word, wd, nv, fP, [&](int i, float x) {
-          const int s = i / 3;
-          reinterpret_cast<float*>(w.P + s)[i - 3 * s] = x;
-        });
-      }
-    });
-  }
+  load_centres<COHERENT>(prow, fP, S, w.P, lane);
   __syncwarp();
   // ---- 2. environment, sphere-major: lane owns spheres base + lane and
   //      base + 32 + lane and sums their terms in registers, cuboid by
@@ -346,34 +386,8 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
     }
   }
   __syncwarp();
-  // ---- 5. cost and packed outputs (one word per lane), then reset acc
-  float local = 0.f;
-  for (int s = lane; s < S; s += 32) local += w.acc[s].x;
-  local = w_c * local + w_s * selfsum;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULL_MASK, local, off);
-  if (out.cost && lane == 0) *out.cost = local;
-  if (out.dist) {
-    dispatch_kind(fD.kind, [&](auto kc) {
-      constexpr int K = decltype(kc)::value;
-      for (int wd = lane; wd < out.dist_words; wd += 32)
-        out.dist[wd] = pack_word_t<K>(wd, S, fD, [&](int i) { return w.acc[i].x; });
-    });
-  }
-  if (out.grad) {
-    const int nv = 3 * S;
-    dispatch_kind(fG.kind, [&](auto kc) {
-      constexpr int K = decltype(kc)::value;
-      for (int wd = lane; wd < out.grad_words; wd += 32)
-        out.grad[wd] = pack_word_t<K>(wd, nv, fG, [&](int i) {
-          const int s = i / 3;
-          return reinterpret_cast<const float*>(w.acc + s)[1 + i - 3 * s];
-        });
-    });
-  }
-  __syncwarp();
-  for (int s = lane; s < S; s += 32) w.acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncwarp();
+  // ---- 5. cost and packed outputs, then reset acc
+  coll_outputs(w, S, fD, fG, w_c, w_s * selfsum, out, lane);
 }
 
 // ------------------------------------------------------- backward (thread)

@@ -1,0 +1,203 @@
+// Swept-sphere environment cost for trajectory optimisation: the cost whose
+// gradient is the paper's closest_pt_swept tensor (Sec. III-C).  The paper
+// names the tensor but prints no formula; the reading here:
+//   rows are trajectories of `horizon` consecutive configurations; row h
+//   sweeps each sphere toward row h' = h+1 (h' = h on the last row) at K
+//   points p_k = c_h + a_k (c_h' - c_h), a_k = k/K;
+//   D_s = sum_k sum_o max(0, r_s + eta - d_o(p_k)),  C = w_c sum_s D_s;
+//   G = d(sum of C over the trajectory)/dc_h: (1 - a_k) times the hinge
+//   gradient at the row's own points (1 on the last row, whose points do
+//   not move with a next row) plus a_k times it at the previous row's points.
+// With K = 1 this is the environment term of vapr_collision_cost exactly.
+//
+// One warp per configuration: the warp decodes its own, the next and the
+// previous P rows into shared memory; each lane owns up to two spheres and,
+// point by point, runs the sphere-major cuboid loop of the collision stage
+// (bounding test, exact distance where it passes), weighting each point's
+// gradient.  The previous row's points are recomputed rather than exchanged,
+// so no two warps write the same row.  Deterministic.
+#include "stages.cuh"
+
+namespace vapr {
+
+constexpr int SW_WARPS = 8;
+
+struct SweptArgs {
+  RobotArgs r;
+  SceneArgs sc;
+  float eta, w_c;
+  Packed pos, dist, grad;
+  float* cost;
+  int64_t n;
+  int horizon, samples;
+};
+
+__host__ __device__ inline void carve_swept(Bump& b, const RobotArgs& r, int O, RobotSm& rb, SceneSm& sm,
+                                            CollWarp& w_mine, float4*& Pn, float4*& Pp, int mine) {
+  carve_robot(b, r.J, r.S, rb);
+  carve_scene(b, O, 0, sm);
+  for (int w = 0; w < SW_WARPS; ++w) {
+    CollWarp t;
+    carve_coll_warp(b, r.S, r.J, t);
+    float4* n = b.take<float4>(r.S);
+    float4* p = b.take<float4>(r.S);
+    if (w == mine) {
+      w_mine = t;
+      Pn = n;
+      Pp = p;
+    }
+  }
+}
+
+// Hinge terms of the point (x, radius x.w) against every cuboid, into t.
+__device__ __forceinline__ void point_terms(const SceneSm& m, int O, const float4& xa, bool va,
+                                            const float4& xb, bool vb, float eta, float w_c, float4& ta,
+                                            float4& tb) {
+  for (int o = 0; o < O; ++o) {
+    const float4 C = m.cubC[o];
+    const float ax = xa.x - C.x, ay = xa.y - C.y, az = xa.z - C.z, sa = xa.w + C.w;
+    const float bx = xb.x - C.x, by = xb.y - C.y, bz = xb.z - C.z, sb = xb.w + C.w;
+    const bool na = va && fmaf(ax, ax, fmaf(ay, ay, az * az)) < sa * sa;
+    const bool nb = vb && fmaf(bx, bx, fmaf(by, by, bz * bz)) < sb * sb;
+    if (__any_sync(FULL_MASK, na || nb)) {
+      if (na) box_term(m, o, xa, eta, w_c, ta);
+      if (nb) box_term(m, o, xb, eta, w_c, tb);
+    }
+  }
+}
+
+__device__ __forceinline__ float4 lerp4(const float4& c, const float4& d, float a) {
+  return make_float4(fmaf(a, d.x - c.x, c.x), fmaf(a, d.y - c.y, c.y), fmaf(a, d.z - c.z, c.z), c.w);
+}
+
+__global__ void __launch_bounds__(SW_WARPS * 32) swept_kernel(SweptArgs a) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Bump b(smem4);
+  RobotSm rb;
+  SceneSm sm;
+  CollWarp w;
+  float4 *Pn, *Pp;
+  carve_swept(b, a.r, a.sc.O, rb, sm, w, Pn, Pp, wid);
+  load_robot(a.r, rb);
+  RobotArgs r0 = a.r;
+  r0.NP = 0;
+  load_scene(r0, a.sc, a.eta, 0.f, sm);
+  init_coll_warp(a.r, w, lane);
+  for (int s = lane; s < a.r.S; s += 32) {
+    Pn[s] = w.P[s];
+    Pp[s] = w.P[s];
+  }
+  __syncthreads();
+
+  const int S = a.r.S, O = a.sc.O, K = a.samples;
+  const float invK = 1.f / (float)K;
+  CollOut out;
+  out.dist_words = (int)(a.dist.stride / 4);
+  out.grad_words = (int)(a.grad.stride / 4);
+  for (int64_t c = blockIdx.x * (int64_t)SW_WARPS + wid; c < a.n; c += (int64_t)gridDim.x * SW_WARPS) {
+    const int h = (int)(c % a.horizon);
+    const bool last = h + 1 == a.horizon, first = h == 0;
+    auto row = [&](int64_t cc) { return reinterpret_cast<const uint32_t*>(a.pos.ptr + cc * a.pos.stride); };
+    load_centres<false>(row(c), a.pos.f, S, w.P, lane);
+    if (!last) load_centres<false>(row(c + 1), a.pos.f, S, Pn, lane);
+    if (!first) load_centres<false>(row(c - 1), a.pos.f, S, Pp, lane);
+    __syncwarp();
+    for (int base = 0; base < S; base += 64) {
+      const int sa = base + lane, sb = base + 32 + lane;
+      const bool va = sa < S, vb = sb < S;
+      const float4 ca = va ? w.P[sa] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 cb = vb ? w.P[sb] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 na = !va ? ca : (last ? ca : make_float4(Pn[sa].x, Pn[sa].y, Pn[sa].z, ca.w));
+      const float4 nb = !vb ? cb : (last ? cb : make_float4(Pn[sb].x, Pn[sb].y, Pn[sb].z, cb.w));
+      const float4 pa = va && !first ? make_float4(Pp[sa].x, Pp[sa].y, Pp[sa].z, ca.w) : ca;
+      const float4 pb = vb && !first ? make_float4(Pp[sb].x, Pp[sb].y, Pp[sb].z, cb.w) : cb;
+      float Da = 0.f, Db = 0.f;
+      float3 ga = make_float3(0.f, 0.f, 0.f), gb = ga;
+      for (int k = 0; k < K; ++k) {
+        const float al = (float)k * invK;
+        {  // the row's own points
+          float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
+          point_terms(sm, O, lerp4(ca, na, al), va, lerp4(cb, nb, al), vb, a.eta, a.w_c, ta, tb);
+          const float wo = last ? 1.f : 1.f - al;
+          Da += ta.x;
+          Db += tb.x;
+          ga = make_float3(fmaf(wo, ta.y, ga.x), fmaf(wo, ta.z, ga.y), fmaf(wo, ta.w, ga.z));
+          gb = make_float3(fmaf(wo, tb.y, gb.x), fmaf(wo, tb.z, gb.y), fmaf(wo, tb.w, gb.z));
+        }
+        if (!first && k > 0) {  // the previous row's points move with this row (weight a_k)
+          float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
+          point_terms(sm, O, lerp4(pa, ca, al), va, lerp4(pb, cb, al), vb, a.eta, a.w_c, ta, tb);
+          ga = make_float3(fmaf(al, ta.y, ga.x), fmaf(al, ta.z, ga.y), fmaf(al, ta.w, ga.z));
+          gb = make_float3(fmaf(al, tb.y, gb.x), fmaf(al, tb.z, gb.y), fmaf(al, tb.w, gb.z));
+        }
+      }
+      if (va) w.acc[sa] = make_float4(Da, ga.x, ga.y, ga.z);
+      if (vb) w.acc[sb] = make_float4(Db, gb.x, gb.y, gb.z);
+    }
+    __syncwarp();
+    out.cost = a.cost ? a.cost + c : nullptr;
+    out.dist = a.dist.ptr ? reinterpret_cast<uint32_t*>(a.dist.ptr + c * a.dist.stride) : nullptr;
+    out.grad = a.grad.ptr ? reinterpret_cast<uint32_t*>(a.grad.ptr + c * a.grad.stride) : nullptr;
+    coll_outputs(w, S, a.dist.f, a.grad.f, a.w_c, 0.f, out, lane);
+  }
+}
+
+static cudaError_t launch_swept(const SweptArgs& a, cudaStream_t st) {
+  Bump b(nullptr);
+  RobotSm rb;
+  SceneSm sm;
+  CollWarp w;
+  float4 *Pn, *Pp;
+  carve_swept(b, a.r, a.sc.O, rb, sm, w, Pn, Pp, 0);
+  const size_t smem = b.bytes();
+  const int per_sm = blocks_per_sm((const void*)swept_kernel, SW_WARPS * 32, smem);
+  if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+  const int64_t blocks = (a.n + SW_WARPS - 1) / SW_WARPS;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  swept_kernel<<<(int)(blocks < cap ? blocks : cap), SW_WARPS * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace vapr
+
+using namespace vapr;
+
+extern "C" vapr_status vapr_swept_cost(const vapr_robot* robot, const vapr_scene* scene,
+                                       const vapr_cost_params* params, const void* pos_packed, int64_t n,
+                                       int32_t horizon, int32_t samples, const vapr_format_table* table,
+                                       float* cost, void* dist_packed, void* grad_packed, void* stream) {
+  RobotArgs r;
+  vapr_status v = check_robot(robot, &r);
+  if (v != VAPR_OK) return v;
+  if ((v = check_table(table)) != VAPR_OK) return v;
+  if (!scene || !params) return VAPR_ERR_INVALID_ARG;
+  if (scene->n_cuboids < 0) return VAPR_ERR_INVALID_ARG;
+  if (scene->n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
+  if (scene->n_cuboids > 0 && (!scene->pose || !scene->half_ext)) return VAPR_ERR_INVALID_ARG;
+  if (scene->n_cuboids > 0 && ((uintptr_t)scene->pose % 16 || (uintptr_t)scene->half_ext % 4))
+    return VAPR_ERR_MISALIGNED;
+  if (n < 0 || horizon < 1 || samples < 1) return VAPR_ERR_INVALID_ARG;
+  if (samples > VAPR_MAX_SWEPT_SAMPLES) return VAPR_ERR_TOO_LARGE;
+  if (n % horizon) return VAPR_ERR_INVALID_ARG;
+  if (n == 0) return VAPR_OK;
+  if (!pos_packed) return VAPR_ERR_INVALID_ARG;
+  if ((uintptr_t)pos_packed % 16 || (uintptr_t)dist_packed % 16 || (uintptr_t)grad_packed % 16 ||
+      (uintptr_t)cost % 4)
+    return VAPR_ERR_MISALIGNED;
+  SweptArgs a;
+  a.r = r;
+  a.sc.O = scene->n_cuboids;
+  a.sc.pose = scene->pose;
+  a.sc.half = scene->half_ext;
+  a.eta = params->eta;
+  a.w_c = params->w_coll;
+  a.pos = Packed{(uint8_t*)pos_packed, (int64_t)row_bytes(3 * (int64_t)r.S, table->pos), make_dev_fmt(table->pos)};
+  a.dist = Packed{(uint8_t*)dist_packed, (int64_t)row_bytes(r.S, table->dist), make_dev_fmt(table->dist)};
+  a.grad = Packed{(uint8_t*)grad_packed, (int64_t)row_bytes(3 * (int64_t)r.S, table->grad), make_dev_fmt(table->grad)};
+  a.cost = cost;
+  a.n = n;
+  a.horizon = horizon;
+  a.samples = samples;
+  return cuda_status(launch_swept(a, (cudaStream_t)stream));
+}

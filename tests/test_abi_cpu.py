@@ -191,3 +191,25 @@ def test_surrogate_argument_checks():
     big = B.vapr_scene(B.MAX_CUBOIDS + 1, 0, 4096, 8192)
     assert lib.vapr_surrogate_samples(ctypes.byref(big), ctypes.byref(dom), p, 5, -1.0, 1.0, p, p,
                                       None) == 6
+
+
+def test_swept_argument_checks():
+    lib = B.lib()
+    import numpy as np
+    from paper_2310_07854_gb300 import synth
+    r = synth.make_robot(0)
+    robot = B.vapr_robot(r.n_joints, r.n_spheres, 0, 0, 4096, 8192, 12288, 16384)
+    scene = B.vapr_scene(2, 0, 4096, 8192)
+    params = B.cost_params(synth.CostParams())
+    t = B.to_c_table(F.FP32_TABLE)
+    call = lambda n, H, K, pos=4096: lib.vapr_swept_cost(ctypes.byref(robot), ctypes.byref(scene),
+                                                         ctypes.byref(params), pos, n, H, K,
+                                                         ctypes.byref(t), None, None, None, None)
+    assert call(64, 32, 0) == 1          # no samples
+    assert call(64, 32, 65) == 6         # above VAPR_MAX_SWEPT_SAMPLES
+    assert call(63, 32, 4) == 1          # n not a multiple of the horizon
+    assert call(64, 0, 4) == 1
+    assert call(0, 32, 4) == 0
+    assert call(64, 32, 4, pos=4104) == 3
+    assert lib.vapr_swept_cost(ctypes.byref(robot), None, ctypes.byref(params), 4096, 64, 32, 4,
+                               ctypes.byref(t), None, None, None, None) == 1
