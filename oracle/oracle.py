@@ -75,6 +75,9 @@ def _load():
             "or_mlp_forward_bf16act": (None, [P, i32, P, i64, P]),
             "or_mlp_grads": (dbl, [P, i32, P, P, i64, dbl, P]),
             "or_swept": (None, [i32, P, i32, P, P, dbl, dbl, P, i64, i32, i32, P, P, P, P, dbl]),
+            "or_ik_costs": (None, [i32, P, i32, P, P, i32, P, i32, P, P, dbl, dbl, dbl, dbl, dbl, dbl,
+                                   dbl, P, P, P, P, i64, P, P]),
+            "or_lbfgs_direction": (None, [i32, i32, P, P, P, P]),
             "or_num_threads": (i32, []),
         }
         for name, (res, args) in sig.items():
@@ -291,3 +294,87 @@ def mlp_grads(params, x, y, H: int = 256, over_weight: float = 1.0):
     g = np.empty(mlp_param_count(H), np.float64)
     loss = _load().or_mlp_grads(_p(params), H, _p(x), _p(y), x.shape[0], float(over_weight), _p(g))
     return float(loss), g
+
+
+# ------------------------------------------------------------- IK iteration
+def ik_costs(robot, scene, params, ik, goal, q):
+    """Total cost [n] and gradient [n, J] of configurations q against goals
+    [n, 12]; ik has w_pos, w_rot, w_bound, q_lo [J], q_hi [J]."""
+    q = _c(q, np.float32).reshape(-1, robot.joint_fixed.shape[0])
+    n, nj = q.shape
+    goal = _c(goal, np.float32).reshape(n, 12)
+    pairs = _c(robot.pairs, np.int32).reshape(-1, 2)
+    cost = np.empty(n, np.float64)
+    grad = np.empty((n, nj), np.float64)
+    _load().or_ik_costs(nj, _p(_c(robot.joint_fixed, np.float32)), robot.sphere_local.shape[0],
+                        _p(_c(robot.sphere_local, np.float32)), _p(_c(robot.sphere_link, np.int32)),
+                        pairs.shape[0], _p(pairs), scene.pose.shape[0], _p(_c(scene.pose, np.float32)),
+                        _p(_c(scene.half_ext, np.float32)), params.eta, params.eta_self, params.w_coll,
+                        params.w_self, ik.w_pos, ik.w_rot, ik.w_bound,
+                        _p(_c(ik.q_lo, np.float32)), _p(_c(ik.q_hi, np.float32)), _p(goal), _p(q), n,
+                        _p(cost), _p(grad))
+    return cost, grad
+
+
+def lbfgs_direction(s, y, g):
+    """-H g from stored pairs s, y [m, dim] (oldest first)."""
+    g = _c(g, np.float64)
+    dim = g.shape[0]
+    s = _c(s, np.float64).reshape(-1, dim)
+    y = _c(y, np.float64).reshape(-1, dim)
+    d = np.empty(dim, np.float64)
+    _load().or_lbfgs_direction(dim, s.shape[0], _p(s), _p(y), _p(g), _p(d))
+    return d
+
+
+def ik_initial_direction(g, step0: float):
+    """Steepest descent scaled so that the largest joint move at step 1 is step0."""
+    g = np.asarray(g, np.float64)
+    return -g * (step0 / max(np.max(np.abs(g)), 1e-30))
+
+
+def ik_iterate(robot, scene, params, ik, goal, q0, iters: int):
+    """Batched IK optimisation in FP64 following Sec. III-B's iteration: N
+    step scales along the direction, costs and gradients of every candidate,
+    the lowest-cost candidate kept (a line search over the scales), then the
+    L-BFGS direction from the updated history.  A step whose best scale is 0
+    clears the history and restarts from steepest descent.  Candidates are
+    rounded to float32 before evaluation, as a float32 solver holds them.
+    ik: w_pos, w_rot, w_bound, q_lo, q_hi, scales, history, step0.
+    Returns dict(q [iters+1, n, J], cost [iters+1, n], pick [iters, n])."""
+    q = np.asarray(q0, np.float64).copy()
+    n, J = q.shape
+    goal = np.asarray(goal, np.float32)
+    f, g = ik_costs(robot, scene, params, ik, goal, q.astype(np.float32))
+    d = np.stack([ik_initial_direction(g[i], ik.step0) for i in range(n)])
+    hist = [[] for _ in range(n)]
+    scales = np.asarray(ik.scales, np.float64)
+    N = len(scales)
+    qs, fs, picks = [q.copy()], [f.copy()], []
+    for _ in range(iters):
+        cand = (q[:, None, :] + scales[None, :, None] * d[:, None, :]).astype(np.float32)
+        fc, gc = ik_costs(robot, scene, params, ik, np.repeat(goal, N, 0), cand.reshape(-1, J))
+        fc, gc = fc.reshape(n, N), gc.reshape(n, N, J)
+        pick = np.argmin(fc, axis=1)
+        for i in range(n):
+            k = pick[i]
+            qn, gn = cand[i, k].astype(np.float64), gc[i, k]
+            if scales[k] == 0.0:
+                hist[i] = []
+                d[i] = ik_initial_direction(gn, ik.step0)
+            else:
+                s, y = qn - q[i], gn - g[i]
+                if s @ y > 0.0:
+                    hist[i].append((s, y))
+                    hist[i] = hist[i][-ik.history:]
+                if hist[i]:
+                    S = np.array([h[0] for h in hist[i]])
+                    Y = np.array([h[1] for h in hist[i]])
+                    d[i] = lbfgs_direction(S, Y, gn)
+                else:
+                    d[i] = ik_initial_direction(gn, ik.step0)
+            q[i], g[i], f[i] = qn, gn, fc[i, k]
+        qs.append(q.copy())
+        fs.append(f.copy())
+        picks.append(pick)
+    return {"q": np.array(qs), "cost": np.array(fs), "pick": np.array(picks)}

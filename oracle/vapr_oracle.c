@@ -643,3 +643,100 @@ double or_mlp_grads(const float* params, int H, const float* x, const float* y, 
   free(buf);
   return loss;
 }
+
+/* ========================================================================= */
+/* IK optimisation: total cost, gradient, and the L-BFGS direction. */
+
+void or_ik_costs(int nj, const float* joint_fixed, int ns, const float* sphere_local,
+                 const int32_t* sphere_link, int npairs, const int32_t* pairs, int no,
+                 const float* pose, const float* half, double eta, double eta_s, double w_c,
+                 double w_s, double w_pos, double w_rot, double w_bound, const float* q_lo,
+                 const float* q_hi, const float* goal, const float* q, int64_t n, double* cost,
+                 double* grad) {
+  double* pos = (double*)malloc(sizeof(double) * 3 * (size_t)ns * (size_t)n);
+  double* ccost = (double*)malloc(sizeof(double) * (size_t)n);
+  double* dist = (double*)malloc(sizeof(double) * (size_t)ns * (size_t)n);
+  double* g = (double*)malloc(sizeof(double) * 3 * (size_t)ns * (size_t)n);
+  or_fk(nj, joint_fixed, ns, sphere_local, sphere_link, q, n, NULL, pos);
+  or_collision(ns, sphere_local, npairs, pairs, no, pose, half, eta, eta_s, w_c, w_s, pos, n, ccost,
+               dist, g, NULL, 0.0);
+  or_backward(nj, joint_fixed, ns, sphere_local, sphere_link, q, g, NULL, n, grad);
+#pragma omp parallel
+  {
+    double* T = (double*)malloc(sizeof(double) * 16 * (size_t)nj);
+#pragma omp for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+      const float* qc = q + (int64_t)nj * c;
+      const float* gl = goal + 12 * c;
+      chain(nj, joint_fixed, qc, T);
+      const double* E = T + 16 * (nj - 1);
+      double dt[3], dR[9], total = ccost[c];
+      for (int i = 0; i < 3; ++i) dt[i] = E[4 * i + 3] - (double)gl[9 + i];
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) dR[3 * i + k] = E[4 * i + k] - (double)gl[3 * i + k];
+      for (int i = 0; i < 3; ++i) total += w_pos * dt[i] * dt[i];
+      for (int i = 0; i < 9; ++i) total += w_rot * dR[i] * dR[i];
+      for (int j = 0; j < nj; ++j) {
+        const double* Tj = T + 16 * j;
+        const double a[3] = {Tj[2], Tj[6], Tj[10]}, o[3] = {Tj[3], Tj[7], Tj[11]};
+        const double rel[3] = {E[3] - o[0], E[7] - o[1], E[11] - o[2]};
+        const double vt[3] = {a[1] * rel[2] - a[2] * rel[1], a[2] * rel[0] - a[0] * rel[2],
+                              a[0] * rel[1] - a[1] * rel[0]};
+        double gj = 0.0;
+        for (int i = 0; i < 3; ++i) gj += 2.0 * w_pos * dt[i] * vt[i];
+        /* dR/dq_j = [a]x R: column k of R rotates as a x R_k */
+        for (int k = 0; k < 3; ++k) {
+          const double Rk[3] = {E[k], E[4 + k], E[8 + k]};
+          const double v[3] = {a[1] * Rk[2] - a[2] * Rk[1], a[2] * Rk[0] - a[0] * Rk[2],
+                               a[0] * Rk[1] - a[1] * Rk[0]};
+          for (int i = 0; i < 3; ++i) gj += 2.0 * w_rot * dR[3 * i + k] * v[i];
+        }
+        const double qj = qc[j];
+        if (qj > q_hi[j]) {
+          total += w_bound * (qj - q_hi[j]) * (qj - q_hi[j]);
+          gj += 2.0 * w_bound * (qj - q_hi[j]);
+        } else if (qj < q_lo[j]) {
+          total += w_bound * (q_lo[j] - qj) * (q_lo[j] - qj);
+          gj -= 2.0 * w_bound * (q_lo[j] - qj);
+        }
+        grad[(int64_t)nj * c + j] += gj;
+      }
+      cost[c] = total;
+    }
+    free(T);
+  }
+  free(pos);
+  free(ccost);
+  free(dist);
+  free(g);
+}
+
+void or_lbfgs_direction(int dim, int m, const double* s, const double* y, const double* g,
+                        double* d) {
+  double alpha[64], rho[64];
+  for (int i = 0; i < dim; ++i) d[i] = -g[i];
+  for (int k = m - 1; k >= 0; --k) { /* newest to oldest */
+    double sy = 0.0, sq = 0.0;
+    for (int i = 0; i < dim; ++i) {
+      sy += s[k * dim + i] * y[k * dim + i];
+      sq += s[k * dim + i] * d[i];
+    }
+    rho[k] = 1.0 / sy;
+    alpha[k] = rho[k] * sq;
+    for (int i = 0; i < dim; ++i) d[i] -= alpha[k] * y[k * dim + i];
+  }
+  if (m > 0) {
+    double sy = 0.0, yy = 0.0;
+    for (int i = 0; i < dim; ++i) {
+      sy += s[(m - 1) * dim + i] * y[(m - 1) * dim + i];
+      yy += y[(m - 1) * dim + i] * y[(m - 1) * dim + i];
+    }
+    for (int i = 0; i < dim; ++i) d[i] *= sy / yy;
+  }
+  for (int k = 0; k < m; ++k) { /* oldest to newest */
+    double yr = 0.0;
+    for (int i = 0; i < dim; ++i) yr += y[k * dim + i] * d[i];
+    const double beta = rho[k] * yr;
+    for (int i = 0; i < dim; ++i) d[i] += (alpha[k] - beta) * s[k * dim + i];
+  }
+}

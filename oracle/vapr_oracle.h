@@ -111,6 +111,26 @@ void or_swept(int ns, const float* sphere_local, int no, const float* pose, cons
               double eta, double w_c, const double* pos, int64_t n, int horizon, int samples,
               double* cost, double* dist, double* grad, int32_t* kink, double kink_eps);
 
+/* ---- IK optimisation iteration (Sec. III-B, iteration steps 1-7) ---------- */
+/* Total cost of configurations q [n][nj] against end-effector goals
+ * goal [n][12] (row-major R*, then t*; the end effector is the frame T_nj):
+ *   collision cost (or_collision on the FK sphere centres)
+ *   + w_pos |t - t*|^2 + w_rot |R - R*|_F^2
+ *   + w_bound sum_j (max(0, q_j - hi_j)^2 + max(0, lo_j - q_j)^2),
+ * and its gradient with respect to q (backward pass for the collision
+ * part; for the pose part dt/dq_j = a_j x (t - o_j), dR/dq_j = [a_j]x R). */
+void or_ik_costs(int nj, const float* joint_fixed, int ns, const float* sphere_local,
+                 const int32_t* sphere_link, int npairs, const int32_t* pairs, int no,
+                 const float* pose, const float* half, double eta, double eta_s, double w_c,
+                 double w_s, double w_pos, double w_rot, double w_bound, const float* q_lo,
+                 const float* q_hi, const float* goal, const float* q, int64_t n, double* cost,
+                 double* grad);
+/* L-BFGS direction d = -H g by the two-loop recursion over the m stored
+ * pairs (s_i, y_i), oldest first ([m][dim] each), with H0 = gamma I,
+ * gamma = s.y / y.y of the newest pair; m = 0 gives d = -g. */
+void or_lbfgs_direction(int dim, int m, const double* s, const double* y, const double* g,
+                        double* d);
+
 /* ---- scene signed distance (surrogate labels) ----------------------------- */
 /* sdf(p) = min_o d_o(p) */
 void or_scene_sdf(int no, const float* pose, const float* half,
