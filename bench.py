@@ -294,6 +294,62 @@ def swept_leg(w, ev32, n, args, flush, torch, samples=4):
     return out
 
 
+def ik_leg(w, ev32, args, torch, n_seeds=4096, iters=50):
+    """Batched IK (Sec. III-B iteration) on the workload's scene: n_seeds
+    seeds x 8 step scales = one particle-sized batch of candidate
+    configurations per iteration; goals are end-effector poses of random
+    configurations.  The iterations run as one captured CUDA graph."""
+    from paper_2310_07854_gb300 import binding as B
+    from paper_2310_07854_gb300 import ik as IK
+    J = w.robot.n_joints
+    goal_q = torch.as_tensor(synth.make_q(4242, n_seeds) * 0.8, device="cuda")
+    xf = B.alloc_packed(n_seeds, 12 * J, F.FP32)
+    pos = B.alloc_packed(n_seeds, 3 * w.robot.n_spheres, F.FP32)
+    B.vapr_fk(ev32.robot, goal_q, n_seeds, F.FP32_TABLE, pos, xf)
+    goal = xf.view(torch.float32)[:, 12 * (J - 1):12 * J].contiguous()
+    q0 = torch.as_tensor(synth.make_q(4343, n_seeds) * 0.8, device="cuda")
+    s = IK.IkSolver(ev32.robot, ev32.scene, w.params, n_seeds)
+    q = q0.clone()
+    s.init(goal, q)
+    f0 = s.cost.clone()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    qg = q0.clone()
+    s.init(goal, qg)
+    s.step()  # warm the launch caches before capture
+    qg.copy_(q0)
+    s.init(goal, qg)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        for _ in range(iters):
+            s.step()
+    qg.copy_(q0)
+    s.init(goal, qg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # final end-effector error
+    B.vapr_fk(ev32.robot, qg, n_seeds, F.FP32_TABLE, pos, xf)
+    fin = xf.view(torch.float32)[:, 12 * (J - 1):12 * J]
+    perr = (fin[:, 9:12] - goal[:, 9:12]).norm(dim=1)
+    rerr = (fin[:, :9] - goal[:, :9]).norm(dim=1)
+    cost = torch.empty(n_seeds, device="cuda")
+    B.vapr_collision_cost(ev32.robot, ev32.scene, w.params, pos, n_seeds, F.FP32_TABLE, cost)
+    return {"seeds": n_seeds, "scales": len(IK.SCALES), "iterations": iters, "ms": ms,
+            "iterations_per_s": iters / (ms / 1000.0),
+            "candidate_configs_per_s": iters * n_seeds * len(IK.SCALES) / (ms / 1000.0),
+            "mean_cost_start_end": [float(f0.mean()), float(s.cost.mean())],
+            "position_error_m_median": float(perr.median()),
+            "frac_position_within_1cm": float((perr < 0.01).float().mean()),
+            "frac_collision_free": float((cost <= 0).float().mean()),
+            "goal_note": "goals are end-effector poses of random configurations, often themselves in collision "
+                         "in this cluttered scene, so pose and collision terms compete"}
+
+
 def fused_leg(w, q, n, vtable, args, flush, torch):
     """FK, collision and backward fused per tile in one persistent launch
     (the multi-problem kernel on this single problem): P and G never leave
@@ -572,6 +628,7 @@ def main():
     fused = fused_leg(w, q, n, vtable, args, flush, torch)
     ev32.fk(q, n)
     swept = swept_leg(w, ev32, n, args, flush, torch)
+    ik_res = ik_leg(w, ev32, args, torch)
 
     found = None
     if not args.no_search:
@@ -603,6 +660,7 @@ def main():
             "stages": stages,
             "fused_single_launch": fused,
             "swept": swept,
+            "ik": ik_res,
             "vapr_search": found,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,

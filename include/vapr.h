@@ -215,6 +215,56 @@ vapr_status vapr_swept_cost(const vapr_robot* robot, const vapr_scene* scene,
                             int32_t horizon, int32_t samples, const vapr_format_table* table,
                             float* cost, void* dist_packed, void* grad_packed, void* stream);
 
+/* ---- IK optimisation iteration (Sec. III-B, iteration steps 1-7) --------- */
+/* A batch of IK seeds optimised on the GPU around the cost-and-gradient
+ * path.  Each iteration (vapr_ik_step) evaluates every seed at N step
+ * scales along its direction (FK, collision cost, backward pass, then the
+ * pose and bound terms), keeps the lowest-cost scale (the paper's line
+ * search over N), and computes the next L-BFGS direction.  Total cost:
+ *   collision (vapr_collision_cost) + w_pos |t - t*|^2 + w_rot |R - R*|_F^2
+ *   + w_bound sum_j (max(0, q_j - hi_j)^2 + max(0, lo_j - q_j)^2),
+ * (R, t) the last link frame T_J.  When the best scale is 0 the history is
+ * cleared and the direction restarts from steepest descent scaled so that
+ * its largest joint move is step0.  Readings: the paper lists these costs
+ * and steps but prints no formula. */
+#define VAPR_IK_MAX_SCALES 16
+#define VAPR_IK_MAX_HISTORY 16
+
+typedef struct {
+  float w_pos, w_rot, w_bound;
+  float step0;                        /* largest joint move of a restart direction (rad) */
+  int32_t n_scales;                   /* N, 1..VAPR_IK_MAX_SCALES */
+  int32_t history;                    /* L-BFGS pairs kept, 1..VAPR_IK_MAX_HISTORY */
+  float scales[VAPR_IK_MAX_SCALES];   /* step scales, scales[0..N) */
+  const float* q_lo;                  /* device float32 [J] joint limits */
+  const float* q_hi;
+} vapr_ik_params;
+
+/* Workspace of vapr_ik_init / vapr_ik_step for n_seeds seeds: the solver
+ * state (gradient, direction, history) and the N x n_seeds candidates with
+ * their path intermediates.  0 on a bad argument. */
+size_t vapr_ik_workspace_bytes(const vapr_robot* robot, int64_t n_seeds, const vapr_ik_params* ik,
+                               const vapr_format_table* table);
+
+/* Starts the solver at q (device float32 [n_seeds][J]): cost and gradient
+ * at q, steepest-descent direction, empty history.  goal: device float32
+ * [n_seeds][12] (R* row-major, then t*).  cost: NULL or float32 [n_seeds]. */
+vapr_status vapr_ik_init(const vapr_robot* robot, const vapr_scene* scene,
+                         const vapr_cost_params* params, const vapr_ik_params* ik,
+                         const float* goal, const float* q, int64_t n_seeds,
+                         const vapr_format_table* table, void* workspace, size_t workspace_bytes,
+                         float* cost, void* stream);
+
+/* One iteration; q (device float32 [n_seeds][J]) is updated in place.
+ * cost: NULL or float32 [n_seeds] (after the step); pick: NULL or int32
+ * [n_seeds] (index of the kept scale).  The workspace must come from
+ * vapr_ik_init with the same arguments. */
+vapr_status vapr_ik_step(const vapr_robot* robot, const vapr_scene* scene,
+                         const vapr_cost_params* params, const vapr_ik_params* ik,
+                         const float* goal, float* q, int64_t n_seeds,
+                         const vapr_format_table* table, void* workspace, size_t workspace_bytes,
+                         float* cost, int32_t* pick, void* stream);
+
 /* ---- tensor-core GEMM (building block of the learned surrogate) ----------- */
 /* C = A * B^T on the tcgen05 tensor cores (TMA-fed shared memory, FP32
  * accumulation in tensor memory).  A: bfloat16 [M][K], B: bfloat16 [N][K],

@@ -90,6 +90,12 @@ class vapr_surrogate_domain(ctypes.Structure):
                 ("margin", ctypes.c_float)]
 
 
+class vapr_ik_params(ctypes.Structure):
+    _fields_ = [("w_pos", ctypes.c_float), ("w_rot", ctypes.c_float), ("w_bound", ctypes.c_float),
+                ("step0", ctypes.c_float), ("n_scales", ctypes.c_int32), ("history", ctypes.c_int32),
+                ("scales", ctypes.c_float * 16), ("q_lo", ctypes.c_void_p), ("q_hi", ctypes.c_void_p)]
+
+
 class vapr_batch_plan(ctypes.Structure):
     _fields_ = [("opaque", ctypes.c_uint64 * 160)]
 
@@ -138,6 +144,16 @@ SIGNATURES = {
                                        ctypes.POINTER(vapr_cost_params), _P, _i64, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.POINTER(vapr_format_table), _P, _P, _P,
                                        _P]),
+    "vapr_ik_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(vapr_robot), _i64,
+                                                  ctypes.POINTER(vapr_ik_params),
+                                                  ctypes.POINTER(vapr_format_table)]),
+    "vapr_ik_init": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
+                                    ctypes.POINTER(vapr_cost_params), ctypes.POINTER(vapr_ik_params), _P, _P,
+                                    _i64, ctypes.POINTER(vapr_format_table), _P, ctypes.c_size_t, _P, _P]),
+    "vapr_ik_step": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
+                                    ctypes.POINTER(vapr_cost_params), ctypes.POINTER(vapr_ik_params), _P, _P,
+                                    _i64, ctypes.POINTER(vapr_format_table), _P, ctypes.c_size_t, _P, _P,
+                                    _P]),
     "vapr_mlp_state_bytes": (ctypes.c_size_t, []),
     "vapr_mlp_init": (ctypes.c_int, [_P, _P, _P]),
     "vapr_mlp_get_params": (ctypes.c_int, [_P, _P, _P]),
@@ -509,3 +525,41 @@ def vapr_surrogate_collision_cost(robot: DeviceRobot, scene: DeviceScene, params
         ctypes.byref(domain), _ptr(pos_packed), n, ctypes.byref(ct), _ptr(cost),
         _ptr(dist_packed), _ptr(grad_packed), _ptr(estimate), _stream(stream)),
         "vapr_surrogate_collision_cost")
+
+
+# ------------------------------------------------------------- IK iteration
+IK_MAX_SCALES = 16
+
+
+def ik_params(w_pos, w_rot, w_bound, step0, scales, history, q_lo, q_hi) -> vapr_ik_params:
+    """q_lo, q_hi: device float32 tensors [J] (kept alive by the caller)."""
+    p = vapr_ik_params()
+    p.w_pos, p.w_rot, p.w_bound, p.step0 = float(w_pos), float(w_rot), float(w_bound), float(step0)
+    p.n_scales, p.history = len(scales), int(history)
+    for k, a in enumerate(scales):
+        p.scales[k] = float(a)
+    p.q_lo, p.q_hi = _ptr(q_lo), _ptr(q_hi)
+    return p
+
+
+def vapr_ik_workspace_bytes(robot: DeviceRobot, n_seeds: int, ik: vapr_ik_params, table) -> int:
+    ct = to_c_table(table)
+    return int(_load().vapr_ik_workspace_bytes(ctypes.byref(robot.c), n_seeds, ctypes.byref(ik), ctypes.byref(ct)))
+
+
+def vapr_ik_init(robot: DeviceRobot, scene: DeviceScene, params, ik, goal, q, n_seeds, table, workspace,
+                 cost=None, stream=None):
+    ct = to_c_table(table)
+    cp = params if isinstance(params, vapr_cost_params) else cost_params(params)
+    _check(_load().vapr_ik_init(ctypes.byref(robot.c), ctypes.byref(scene.c), ctypes.byref(cp), ctypes.byref(ik),
+                                _ptr(goal), _ptr(q), n_seeds, ctypes.byref(ct), _ptr(workspace),
+                                workspace.numel(), _ptr(cost), _stream(stream)), "vapr_ik_init")
+
+
+def vapr_ik_step(robot: DeviceRobot, scene: DeviceScene, params, ik, goal, q, n_seeds, table, workspace,
+                 cost=None, pick=None, stream=None):
+    ct = to_c_table(table)
+    cp = params if isinstance(params, vapr_cost_params) else cost_params(params)
+    _check(_load().vapr_ik_step(ctypes.byref(robot.c), ctypes.byref(scene.c), ctypes.byref(cp), ctypes.byref(ik),
+                                _ptr(goal), _ptr(q), n_seeds, ctypes.byref(ct), _ptr(workspace),
+                                workspace.numel(), _ptr(cost), _ptr(pick), _stream(stream)), "vapr_ik_step")
