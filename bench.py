@@ -92,21 +92,44 @@ def cpu_baseline(workload_name: str, seconds: float) -> dict:
                       f"{el:.1f} s"}
 
 
+def workload_config(w, world: int) -> dict:
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": w.name if hasattr(w, "name") else None, "global_batch": world * w.n,
+            "trajectories": w.n_traj, "horizon": w.horizon, "spheres": w.robot.n_spheres,
+            "cuboids": w.scene.n_cuboids, "self_pairs": w.robot.n_pairs, "table": str(F.FP32_TABLE),
+            "parallelism": f"replicas{world}",
+            "l2": "flushed before every step (2 x L2 buffer rewritten outside the timed events)"}
+
+
 def run_reference(args):
+    """The oracle as the reference arm: --warmup untimed batches, then
+    --steps timed batches of the workload on the host cores (rank 0 only)."""
     world, rank, _ = replicas.dist_env()
     if rank != 0:
         return
-    cb = cpu_baseline(args.workload, max(args.cpu_seconds, 5.0))
-    steps_time = args.steps * (synth.make_workload(args.workload).n / cb["value"])
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "configs/s",
+    import oracle
+    oracle.build()
+    w = synth.make_workload(args.workload)
+    w.name = args.workload
+    for _ in range(args.warmup):
+        oracle.cost_and_grad(w.robot, w.scene, w.params, w.q)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.cost_and_grad(w.robot, w.scene, w.params, w.q)
+    el = time.perf_counter() - t0
+    value = args.steps * w.n / el
+    cfg = workload_config(w, 1)
+    cfg["l2"] = "n/a (host CPU)"
+    cb = {"value": value, "unit": "configs/s", "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"{args.steps} timed batches of {w.n} configurations of {args.workload} after "
+                    f"{args.warmup} untimed (FP64 FK + collision + backward, OpenMP over configurations), "
+                    f"{el:.1f} s"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "configs/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * steps_time / max(args.steps, 1), "higher_is_better": True,
+            "ms_per_step": 1000.0 * el / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "global_batch": synth.make_workload(args.workload).n,
-                       "l2": "n/a (CPU)"},
-            "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "configs/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": cfg, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "configs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -515,6 +538,7 @@ def main():
     B.lib()
 
     w = synth.make_workload(args.workload)
+    w.name = args.workload
     if args.configs:
         w.q = synth.make_q(500, args.configs)
         w.n_traj = max(1, args.configs // w.horizon)
@@ -648,11 +672,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t32 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "global_batch": world * n, "trajectories": w.n_traj,
-                       "horizon": w.horizon, "spheres": w.robot.n_spheres,
-                       "cuboids": w.scene.n_cuboids, "self_pairs": w.robot.n_pairs,
-                       "table": str(F.FP32_TABLE), "parallelism": f"replicas{world}",
-                       "l2": "flushed before every step (2 x L2 buffer rewritten outside the timed events)"},
+            "config": workload_config(w, world),
             "roofline": roof,
             "vapr": {"table": str(vtable), "value": value_v, "unit": "configs/s",
                      "speedup_vs_fp32": value_v / value, "ms_per_step": tv / args.steps,
