@@ -10,17 +10,20 @@
 //   not move with a next row) plus a_k times it at the previous row's points.
 // With K = 1 this is the environment term of vapr_collision_cost exactly.
 //
-// One warp per configuration: the warp decodes its own, the next and the
-// previous P rows into shared memory; each lane owns up to two spheres and,
-// point by point, runs the sphere-major cuboid loop of the collision stage
-// (bounding test, exact distance where it passes), weighting each point's
-// gradient.  The previous row's points are recomputed rather than exchanged,
-// so no two warps write the same row.  Deterministic.
+// One warp per chunk of SW_CHUNK consecutive rows of one trajectory: the
+// warp walks its rows in order, decoding each P row once (the next row's
+// centres become the current ones).  Lanes own up to two spheres and run the
+// sphere-major cuboid loop of the collision stage at each swept point; a
+// point's gradient goes to its own row with weight 1 - a_k and is carried to
+// the next row with weight a_k, so every point is evaluated once.  The first
+// row of a chunk recomputes the carry from the previous row's points.
+// Deterministic: a row's sums do not depend on where chunks start.
 #include "stages.cuh"
 
 namespace vapr {
 
 constexpr int SW_WARPS = 8;
+constexpr int SW_CHUNK = 8;  // rows per warp
 
 struct SweptArgs {
   RobotArgs r;
@@ -90,33 +93,63 @@ __global__ void __launch_bounds__(SW_WARPS * 32) swept_kernel(SweptArgs a) {
   }
   __syncthreads();
 
-  const int S = a.r.S, O = a.sc.O, K = a.samples;
+  const int S = a.r.S, O = a.sc.O, K = a.samples, H = a.horizon;
   const float invK = 1.f / (float)K;
+  const int64_t chunks_per_traj = (H + SW_CHUNK - 1) / SW_CHUNK;
+  const int64_t n_chunks = (a.n / H) * chunks_per_traj;
+  auto row = [&](int64_t cc) { return reinterpret_cast<const uint32_t*>(a.pos.ptr + cc * a.pos.stride); };
+  float4* cur = w.P;  // centres of the row being finished (.w = radius)
+  float4* nxt = Pn;
   CollOut out;
   out.dist_words = (int)(a.dist.stride / 4);
   out.grad_words = (int)(a.grad.stride / 4);
-  for (int64_t c = blockIdx.x * (int64_t)SW_WARPS + wid; c < a.n; c += (int64_t)gridDim.x * SW_WARPS) {
-    const int h = (int)(c % a.horizon);
-    const bool last = h + 1 == a.horizon, first = h == 0;
-    auto row = [&](int64_t cc) { return reinterpret_cast<const uint32_t*>(a.pos.ptr + cc * a.pos.stride); };
-    load_centres<false>(row(c), a.pos.f, S, w.P, lane);
-    if (!last) load_centres<false>(row(c + 1), a.pos.f, S, Pn, lane);
-    if (!first) load_centres<false>(row(c - 1), a.pos.f, S, Pp, lane);
+  for (int64_t ch = blockIdx.x * (int64_t)SW_WARPS + wid; ch < n_chunks; ch += (int64_t)gridDim.x * SW_WARPS) {
+    const int64_t traj = ch / chunks_per_traj;
+    const int h0 = (int)(ch - traj * chunks_per_traj) * SW_CHUNK;
+    const int h1 = min(H, h0 + SW_CHUNK);
+    const int64_t base_row = traj * H;
+    load_centres<false>(row(base_row + h0), a.pos.f, S, cur, lane);
+    if (h0 > 0) load_centres<false>(row(base_row + h0 - 1), a.pos.f, S, Pp, lane);
     __syncwarp();
-    for (int base = 0; base < S; base += 64) {
-      const int sa = base + lane, sb = base + 32 + lane;
+    // carry into the chunk's first row: the previous row's points, weight
+    // a_k; each lane keeps the carries of its spheres in Pp[s].xyz (the
+    // previous row's centres are no longer needed once read)
+    for (int pass = 0; pass * 64 < S; ++pass) {
+      const int sa = pass * 64 + lane, sb = sa + 32;
       const bool va = sa < S, vb = sb < S;
-      const float4 ca = va ? w.P[sa] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 cb = vb ? w.P[sb] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 na = !va ? ca : (last ? ca : make_float4(Pn[sa].x, Pn[sa].y, Pn[sa].z, ca.w));
-      const float4 nb = !vb ? cb : (last ? cb : make_float4(Pn[sb].x, Pn[sb].y, Pn[sb].z, cb.w));
-      const float4 pa = va && !first ? make_float4(Pp[sa].x, Pp[sa].y, Pp[sa].z, ca.w) : ca;
-      const float4 pb = vb && !first ? make_float4(Pp[sb].x, Pp[sb].y, Pp[sb].z, cb.w) : cb;
-      float Da = 0.f, Db = 0.f;
-      float3 ga = make_float3(0.f, 0.f, 0.f), gb = ga;
-      for (int k = 0; k < K; ++k) {
-        const float al = (float)k * invK;
-        {  // the row's own points
+      float3 c0 = make_float3(0.f, 0.f, 0.f), c1 = c0;
+      if (h0 > 0) {
+        const float4 ca = va ? cur[sa] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 cb = vb ? cur[sb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 pa = va ? make_float4(Pp[sa].x, Pp[sa].y, Pp[sa].z, ca.w) : ca;
+        const float4 pb = vb ? make_float4(Pp[sb].x, Pp[sb].y, Pp[sb].z, cb.w) : cb;
+        for (int k = 1; k < K; ++k) {
+          const float al = (float)k * invK;
+          float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
+          point_terms(sm, O, lerp4(pa, ca, al), va, lerp4(pb, cb, al), vb, a.eta, a.w_c, ta, tb);
+          c0 = make_float3(fmaf(al, ta.y, c0.x), fmaf(al, ta.z, c0.y), fmaf(al, ta.w, c0.z));
+          c1 = make_float3(fmaf(al, tb.y, c1.x), fmaf(al, tb.z, c1.y), fmaf(al, tb.w, c1.z));
+        }
+      }
+      if (va) Pp[sa] = make_float4(c0.x, c0.y, c0.z, Pp[sa].w);
+      if (vb) Pp[sb] = make_float4(c1.x, c1.y, c1.z, Pp[sb].w);
+    }
+    for (int h = h0; h < h1; ++h) {
+      const int64_t c = base_row + h;
+      const bool last = h + 1 == H;
+      if (!last) load_centres<false>(row(c + 1), a.pos.f, S, nxt, lane);
+      __syncwarp();
+      for (int pass = 0; pass * 64 < S; ++pass) {
+        const int sa = pass * 64 + lane, sb = sa + 32;
+        const bool va = sa < S, vb = sb < S;
+        const float4 ca = va ? cur[sa] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 cb = vb ? cur[sb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 na = va && !last ? make_float4(nxt[sa].x, nxt[sa].y, nxt[sa].z, ca.w) : ca;
+        const float4 nb = vb && !last ? make_float4(nxt[sb].x, nxt[sb].y, nxt[sb].z, cb.w) : cb;
+        float Da = 0.f, Db = 0.f;
+        float3 ga = make_float3(0.f, 0.f, 0.f), gb = ga, fa = ga, fb = ga;
+        for (int k = 0; k < K; ++k) {
+          const float al = (float)k * invK;
           float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
           point_terms(sm, O, lerp4(ca, na, al), va, lerp4(cb, nb, al), vb, a.eta, a.w_c, ta, tb);
           const float wo = last ? 1.f : 1.f - al;
@@ -124,22 +157,34 @@ __global__ void __launch_bounds__(SW_WARPS * 32) swept_kernel(SweptArgs a) {
           Db += tb.x;
           ga = make_float3(fmaf(wo, ta.y, ga.x), fmaf(wo, ta.z, ga.y), fmaf(wo, ta.w, ga.z));
           gb = make_float3(fmaf(wo, tb.y, gb.x), fmaf(wo, tb.z, gb.y), fmaf(wo, tb.w, gb.z));
+          if (!last && k > 0) {  // the same point moves with the next row (weight a_k)
+            fa = make_float3(fmaf(al, ta.y, fa.x), fmaf(al, ta.z, fa.y), fmaf(al, ta.w, fa.z));
+            fb = make_float3(fmaf(al, tb.y, fb.x), fmaf(al, tb.z, fb.y), fmaf(al, tb.w, fb.z));
+          }
         }
-        if (!first && k > 0) {  // the previous row's points move with this row (weight a_k)
-          float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
-          point_terms(sm, O, lerp4(pa, ca, al), va, lerp4(pb, cb, al), vb, a.eta, a.w_c, ta, tb);
-          ga = make_float3(fmaf(al, ta.y, ga.x), fmaf(al, ta.z, ga.y), fmaf(al, ta.w, ga.z));
-          gb = make_float3(fmaf(al, tb.y, gb.x), fmaf(al, tb.z, gb.y), fmaf(al, tb.w, gb.z));
+        // own points, then the carry from the previous row; store the next carry
+        if (va) {
+          const float4 cr = Pp[sa];
+          w.acc[sa] = make_float4(Da, ga.x + cr.x, ga.y + cr.y, ga.z + cr.z);
+          Pp[sa] = make_float4(fa.x, fa.y, fa.z, cr.w);
+        }
+        if (vb) {
+          const float4 cr = Pp[sb];
+          w.acc[sb] = make_float4(Db, gb.x + cr.x, gb.y + cr.y, gb.z + cr.z);
+          Pp[sb] = make_float4(fb.x, fb.y, fb.z, cr.w);
         }
       }
-      if (va) w.acc[sa] = make_float4(Da, ga.x, ga.y, ga.z);
-      if (vb) w.acc[sb] = make_float4(Db, gb.x, gb.y, gb.z);
+      __syncwarp();
+      out.cost = a.cost ? a.cost + c : nullptr;
+      out.dist = a.dist.ptr ? reinterpret_cast<uint32_t*>(a.dist.ptr + c * a.dist.stride) : nullptr;
+      out.grad = a.grad.ptr ? reinterpret_cast<uint32_t*>(a.grad.ptr + c * a.grad.stride) : nullptr;
+      coll_outputs(w, S, a.dist.f, a.grad.f, a.w_c, 0.f, out, lane);
+      if (!last) {  // the next row's centres become the current ones
+        float4* t = cur;
+        cur = nxt;
+        nxt = t;
+      }
     }
-    __syncwarp();
-    out.cost = a.cost ? a.cost + c : nullptr;
-    out.dist = a.dist.ptr ? reinterpret_cast<uint32_t*>(a.dist.ptr + c * a.dist.stride) : nullptr;
-    out.grad = a.grad.ptr ? reinterpret_cast<uint32_t*>(a.grad.ptr + c * a.grad.stride) : nullptr;
-    coll_outputs(w, S, a.dist.f, a.grad.f, a.w_c, 0.f, out, lane);
   }
 }
 
@@ -153,7 +198,8 @@ static cudaError_t launch_swept(const SweptArgs& a, cudaStream_t st) {
   const size_t smem = b.bytes();
   const int per_sm = blocks_per_sm((const void*)swept_kernel, SW_WARPS * 32, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-  const int64_t blocks = (a.n + SW_WARPS - 1) / SW_WARPS;
+  const int64_t chunks = (a.n / a.horizon) * ((a.horizon + SW_CHUNK - 1) / SW_CHUNK);
+  const int64_t blocks = (chunks + SW_WARPS - 1) / SW_WARPS;
   const int64_t cap = (int64_t)sm_count() * per_sm;
   swept_kernel<<<(int)(blocks < cap ? blocks : cap), SW_WARPS * 32, smem, st>>>(a);
   return cudaGetLastError();
