@@ -411,7 +411,21 @@ def time_graph(fn, steps, warmup, flush_buf, torch):
     return statistics.mean(ts)
 
 
-def surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind):
+def surrogate_sweep(w, q, n, args, flush, torch, counts=(40, 160, 640)):
+    """Obstacle-count sweep of the surrogate against the exact stage, cuboid
+    density held constant (the scene's half-width grows as O^(1/3))."""
+    from paper_2310_07854_gb300.path import Evaluator
+    out = []
+    for O in counts:
+        scene = synth.make_scene(1 + O, O, extent=0.75 * (O / 40.0) ** (1.0 / 3.0))
+        ev = Evaluator(w.robot, scene, w.params, n, F.FP32_TABLE)
+        r = surrogate_leg(w, ev, q, n, args, flush, torch, None, None, light=True)
+        out.append({"cuboids": O, "extent_m": 0.75 * (O / 40.0) ** (1.0 / 3.0), **r})
+        del ev
+    return out
+
+
+def surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind, light=False):
     """Learned signed-distance surrogate of the workload's scene: trained on
     2M exact distances, then used as the broad phase of the collision stage
     on the workload's sphere centres.  Reports training time and loss, the
@@ -454,6 +468,14 @@ def surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind):
     err = (e - sdf).abs()
     t_exact = time_graph(lambda: ev32.collision(n), args.steps, args.warmup, flush, torch)
     t_gated = time_graph(gated, args.steps, args.warmup, flush, torch)
+    if light:
+        return {"cleared": float(skipped.float().mean()),
+                "clearable": float(((sdf - r) >= sg.domain.margin).float().mean()),
+                "missed_contacts": miss,
+                "equal_to_exact": all(torch.equal(a, b) for a, b in zip(exact, (cost, dist, grad))),
+                "margin_m": sg.domain.margin, "train_s": train_s,
+                "ms": {"exact_collision": t_exact, "gated_collision": t_gated},
+                "speedup_vs_fp32_collision": t_exact / t_gated}
     f = torch.empty(n * S, device="cuda")
     t_net = time_graph(lambda: sg.forward_into(uq, f), args.steps, args.warmup, flush, torch)
     t_sdf = time_graph(lambda: B.vapr_scene_sdf(ev32.scene, c, n * S, sdf), args.steps, args.warmup,
@@ -562,6 +584,13 @@ def main():
     peaks, peak_kind = measured_peaks()
     barrier()
     with ClockSampler(local) as clk:
+        # keep the GPU busy while the sampler starts, so that its samples see
+        # the clocks under this load (untimed)
+        t_end = time.perf_counter() + 0.8
+        while time.perf_counter() < t_end:
+            for _ in range(20):
+                ev32.step(q, n)
+            torch.cuda.synchronize()
         per32 = time_steps(ev32, q, n, args.steps, args.warmup, flush, torch)
         perv = time_steps(evv, q, n, args.steps, args.warmup, flush, torch)
     barrier()
@@ -661,6 +690,7 @@ def main():
     sur = None
     if not args.no_surrogate:
         sur = surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind)
+        sur["obstacle_sweep"] = surrogate_sweep(w, q, n, args, flush, torch)
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
