@@ -287,15 +287,26 @@ def search_leg(w, ev32, q, n, args, flush, torch, per32):
     out = {"budget": "max|C-C32| <= 5% max|C32| and max|J-J32| <= 5% max|J32| (1024 validation configs)",
            "per_tensor_min_bits": {k: v[0] for k, v in per.items()}, "reduced_space": S.space_size(space),
            "evaluations": ev.count, "search_s": search_s}
-    if best is None:
-        return out
-    evb = Evaluator(ev32.robot, ev32.scene, w.params, n, best)
-    pb = time_steps(evb, q, n, args.steps, args.warmup, flush, torch)
-    out.update({"table": str(best), "bits_searched_tensors": sum(getattr(best, k).bits for k in tensors),
+
+    def timed(best, e):
+        evb = Evaluator(ev32.robot, ev32.scene, w.params, n, best)
+        pb = time_steps(evb, q, n, args.steps, args.warmup, flush, torch)
+        return {"table": str(best), "bits_searched_tensors": sum(getattr(best, k).bits for k in tensors),
                 "validation_error": e.error,
                 "configs_per_s": n * args.steps / (sum(pb["step"]) / 1000.0),
                 "speedup_vs_fp32": sum(per32["step"]) / sum(pb["step"]),
-                "stage_ms": {k: statistics.mean(pb[k]) for k in ("fk", "collision", "backward") if pb[k]}})
+                "stage_ms": {k: statistics.mean(pb[k]) for k in ("fk", "collision", "backward") if pb[k]}}
+
+    if best is not None:
+        out.update(timed(best, e))
+    # the same search restricted to formats with a one-instruction converter
+    hw = F.hardware_formats()
+    per_hw = S.per_tensor_search(ev, tensors, candidates=hw)
+    space_hw = S.reduced_space(per_hw, hw)
+    start_hw = F.FormatTable(**{k: space_hw[k][0] for k in tensors})
+    best_hw, e_hw, _ = S.combinatorial_search(ev, space_hw, samples=args.search_samples, seed=0, seeds=[start_hw])
+    if best_hw is not None:
+        out["hardware_formats_only"] = {"reduced_space": S.space_size(space_hw), **timed(best_hw, e_hw)}
     return out
 
 

@@ -126,6 +126,14 @@ def search_set() -> list[Fmt]:
     return out
 
 
+def hardware_formats() -> list[Fmt]:
+    """Members of the search set that sm_103a converts with one cvt
+    instruction (FP32, FP16, BF16, E4M3, E5M2, E3M2, E2M3, E2M1); the rest
+    use the generic integer converter."""
+    hw = {(2, 1), (2, 3), (3, 2), (4, 3), (5, 2), (5, 10), (8, 7), (8, 23)}
+    return [f for f in search_set() if (f.E, f.M) in hw]
+
+
 def formats_at_least(bits: int) -> list[Fmt]:
     """Candidates a per-tensor search result of ``bits`` leaves (Sec. V-A)."""
     return [f for f in search_set() if f.bits >= bits]
