@@ -36,7 +36,7 @@ from paper_2310_07854_gb300 import synth  # noqa: E402
 
 WORKLOAD = "particle_32768"
 VAPR_TABLE = "P=E5M10,D=E2M1,G=E2M1,J=E4M3"
-METRIC = "configs/s for FK+collision cost+grad"
+METRIC = "configs/s for FK+collision cost+grad, % of HBM roofline; VaPr vs FP32 at stated err"
 
 
 def parse_args():
