@@ -82,3 +82,18 @@ def test_solver_descends():
         prev = s.cost.clone()
     assert float(s.cost.mean()) < 0.25 * float(f0.mean())
     assert B.vapr_device_error() == 0
+
+
+def test_reduced_table_descends():
+    """The solver with the path's tensors in reduced formats still descends."""
+    from paper_2310_07854_gb300 import formats as F
+    w, goal, q0 = _problem(512, seed=21)
+    rd, sd = B.DeviceRobot(w.robot), B.DeviceScene(w.scene)
+    s = IK.IkSolver(rd, sd, w.params, len(q0), table=F.FormatTable.parse("P=E5M10,D=E2M1,G=E4M3,J=E5M10"))
+    q = to_dev(q0)
+    s.init(to_dev(goal), q)
+    f0 = float(s.cost.mean())
+    for _ in range(20):
+        s.step()
+    assert float(s.cost.mean()) < 0.5 * f0
+    assert B.vapr_device_error() == 0

@@ -317,3 +317,24 @@ def test_trained_surrogate_config5():
     assert untrained["misses"] > 0 and not untrained["equal_to_exact"]
     assert trained["cleared"] >= 0.5 * trained["clearable"]
     assert B.vapr_device_error() == 0
+
+
+def test_estimates_from_packed_positions():
+    """P in E5M10: the estimates equal the network at the decoded centres."""
+    import torch
+    w = synth.make_workload("sweep_1024")
+    rd, sd = B.DeviceRobot(w.robot), B.DeviceScene(w.scene)
+    S = w.robot.n_spheres
+    t = F.FormatTable(pos=F.FP16)
+    pos = B.alloc_packed(w.n, 3 * S, F.FP16)
+    B.vapr_fk(rd, to_dev(w.q), w.n, t, pos)
+    sg = SG.Surrogate(sd, synth.init_mlp_params(3))
+    est = sg.collision_cost(rd, w.params, pos, w.n, t).reshape(-1)
+    dec = torch.empty((w.n, 3 * S), device="cuda")
+    B.vapr_unpack(pos, w.n, 3 * S, F.FP16, dec)
+    c = dec.reshape(-1, 3).contiguous()
+    u, _ = sg.samples(c)
+    inside = (c >= torch.as_tensor(sg.lo, device="cuda")).all(1) & (c <= torch.as_tensor(sg.hi, device="cuda")).all(1)
+    f = sg.forward(u)
+    assert inside.float().mean() > 0.5
+    assert torch.equal(est[inside], f[inside])

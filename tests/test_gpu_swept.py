@@ -94,3 +94,21 @@ def test_reduced_formats_round_the_fp32_results():
     B.vapr_pack(g32.view(torch.float32)[:, :3 * S].contiguous(), w.n, 3 * S, F.E4M3, gp)
     assert torch.equal(dp, dr) and torch.equal(gp, gr)
     assert B.vapr_device_error() == 0
+
+
+def test_reduced_position_format_matches_oracle_on_decoded_centres():
+    """P stored in E5M10: the swept cost equals the FP64 swept cost of the
+    decoded (rounded) centres to the FP32 tolerance."""
+    import torch
+    w, robot, rd, sd, _ = _setup()
+    S = robot.n_spheres
+    t = F.FormatTable(pos=F.FP16)
+    pos = B.alloc_packed(w.n, 3 * S, F.FP16)
+    B.vapr_fk(rd, to_dev(w.q), w.n, t, pos)
+    c, d, g = _swept(rd, sd, w, pos, w.horizon, 3, t)
+    dec = torch.empty((w.n, 3 * S), device="cuda")
+    B.vapr_unpack(pos, w.n, 3 * S, F.FP16, dec)
+    p64 = dec.cpu().numpy().astype(np.float64).reshape(w.n, S, 3)
+    ref = oracle.swept(robot, w.scene, w.params, p64, w.horizon, 3, kink_eps=KINK_EPS)
+    got_c = c.cpu().numpy()
+    assert np.max(np.abs(got_c - ref["cost"])) <= REL_TOL * np.max(np.abs(ref["cost"]))
