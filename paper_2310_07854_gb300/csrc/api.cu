@@ -109,8 +109,11 @@ int blocks_per_sm(const void* fn, int threads, size_t smem) {
   for (const auto& r : raised) done |= (r.first == fn && r.second == dev);
   if (!done) {  // allow up to the device's opt-in maximum once; launches use less
     int optin = 0;
+    cudaFuncAttributes fa;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess) {
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {  // minus static shared
       cudaGetLastError();  // clear it: a later launch check must not see this
       return -1;
     }
