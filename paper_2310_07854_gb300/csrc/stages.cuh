@@ -173,15 +173,43 @@ __device__ inline void load_scene(const RobotArgs& r, const SceneArgs& sc, float
 }
 
 // One warp's working set for one configuration.
+constexpr int ACT_CAP = 64;  // warp list of active self pairs awaiting their gradient update
+
 struct CollWarp {
   float4* P;    // [S] (x, y, z, r)
   float4* acc;  // [S] (D, gx, gy, gz)
+  float4* act;  // [ACT_CAP] active self pairs: (bits of i | j << 16, u) with u = w_s (c_i - c_j)/|c_i - c_j|
 };
 
 __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp& w) {
   (void)J;
   w.P = b.take<float4>(S);
   w.acc = b.take<float4>(S);
+  w.act = b.take<float4>(ACT_CAP);
+}
+
+// Applies the listed active self pairs to acc, sphere-major: each lane takes
+// its spheres (up to two per 64) and walks the list in order, subtracting u
+// where it is the pair's first sphere and adding it where it is the second,
+// so every sphere receives its self terms in pair order.
+__device__ __forceinline__ void apply_self_pairs(const CollWarp& w, int S, int n_act, int lane) {
+  for (int base = 0; base < S; base += 64) {
+    const int sa = base + lane, sb = sa + 32;
+    float4 a = sa < S ? w.acc[sa] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 b = sb < S ? w.acc[sb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = 0; e < n_act; ++e) {
+      const float4 t = w.act[e];
+      const uint32_t ij = __float_as_uint(t.x);
+      const int i = (int)(ij & 0xffffu), j = (int)(ij >> 16);
+      if (i == sa) { a.y -= t.y; a.z -= t.z; a.w -= t.w; }
+      if (j == sa) { a.y += t.y; a.z += t.z; a.w += t.w; }
+      if (i == sb) { b.y -= t.y; b.z -= t.z; b.w -= t.w; }
+      if (j == sb) { b.y += t.y; b.z += t.z; b.w += t.w; }
+    }
+    if (sa < S) w.acc[sa] = a;
+    if (sb < S) w.acc[sb] = b;
+  }
+  __syncwarp();
 }
 
 // Radii into P[].w and zero accumulators (once per robot).
@@ -341,8 +369,10 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
     if (sb < S) w.acc[sb] = accb;
   }
   __syncwarp();
-  // ---- 4. self-collision over the pair list
+  // ---- 4. self-collision over the pair list; active pairs are listed and
+  //      their gradients applied sphere-major in pair order
   float selfsum = 0.f;
+  int n_act = 0;
   for (int pb = 0; pb < NP; pb += 32) {
     const int p = pb + lane;
     bool act = false;
@@ -366,27 +396,21 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
         uz = dz * inv;
       }
     }
-    unsigned am = __ballot_sync(FULL_MASK, act);
-    if (act) selfsum += pen;
-    while (am) {  // active pairs are rare: apply them one lane at a time, in pair order
-      const int l = __ffs(am) - 1;
-      if (lane == l) {
-        float4 vi = w.acc[i];
-        vi.y -= ux;
-        vi.z -= uy;
-        vi.w -= uz;
-        w.acc[i] = vi;
-        float4 vj = w.acc[j];
-        vj.y += ux;
-        vj.z += uy;
-        vj.w += uz;
-        w.acc[j] = vj;
-      }
+    const unsigned am = __ballot_sync(FULL_MASK, act);
+    if (act) {  // list the active pair (pair order = lane order within the chunk)
+      selfsum += pen;
+      w.act[n_act + __popc(am & ((1u << lane) - 1u))] =
+          make_float4(__uint_as_float((uint32_t)i | ((uint32_t)j << 16)), ux, uy, uz);
+    }
+    n_act += __popc(am);
+    if (n_act > ACT_CAP - 32) {  // the next chunk might not fit: apply what is listed
       __syncwarp();
-      am &= am - 1u;
+      apply_self_pairs(w, S, n_act, lane);
+      n_act = 0;
     }
   }
   __syncwarp();
+  if (n_act > 0) apply_self_pairs(w, S, n_act, lane);
   // ---- 5. cost and packed outputs, then reset acc
   coll_outputs(w, S, fD, fG, w_c, w_s * selfsum, out, lane);
 }
