@@ -328,6 +328,31 @@ def swept_leg(w, ev32, n, args, flush, torch, samples=4):
     return out
 
 
+def ik_pose_only(w, ev32, torch, n_seeds=4096, iters=100):
+    """The same solver with the collision weights at zero: how well the
+    pose and bound terms alone are met (the L-BFGS solver's own accuracy)."""
+    import dataclasses
+    from paper_2310_07854_gb300 import binding as B
+    from paper_2310_07854_gb300 import ik as IK
+    J = w.robot.n_joints
+    params = dataclasses.replace(w.params, w_coll=0.0, w_self=0.0)
+    goal_q = torch.as_tensor(synth.make_q(4242, n_seeds) * 0.8, device="cuda")
+    xf = B.alloc_packed(n_seeds, 12 * J, F.FP32)
+    pos = B.alloc_packed(n_seeds, 3 * w.robot.n_spheres, F.FP32)
+    B.vapr_fk(ev32.robot, goal_q, n_seeds, F.FP32_TABLE, pos, xf)
+    goal = xf.view(torch.float32)[:, 12 * (J - 1):12 * J].contiguous()
+    q = torch.as_tensor(synth.make_q(4343, n_seeds) * 0.8, device="cuda")
+    s = IK.IkSolver(ev32.robot, ev32.scene, params, n_seeds)
+    s.init(goal, q)
+    s.solve(iters)
+    B.vapr_fk(ev32.robot, q, n_seeds, F.FP32_TABLE, pos, xf)
+    fin = xf.view(torch.float32)[:, 12 * (J - 1):12 * J]
+    perr = (fin[:, 9:12] - goal[:, 9:12]).norm(dim=1)
+    rerr = (fin[:, :9] - goal[:, :9]).norm(dim=1)
+    return {"iterations": iters, "position_error_m_median": float(perr.median()),
+            "frac_within_1cm_and_0.05_rot": float(((perr < 0.01) & (rerr < 0.05)).float().mean())}
+
+
 def ik_leg(w, ev32, args, torch, n_seeds=4096, iters=50):
     """Batched IK (Sec. III-B iteration) on the workload's scene: n_seeds
     seeds x 8 step scales = one particle-sized batch of candidate
@@ -381,7 +406,8 @@ def ik_leg(w, ev32, args, torch, n_seeds=4096, iters=50):
             "frac_position_within_1cm": float((perr < 0.01).float().mean()),
             "frac_collision_free": float((cost <= 0).float().mean()),
             "goal_note": "goals are end-effector poses of random configurations, often themselves in collision "
-                         "in this cluttered scene, so pose and collision terms compete"}
+                         "in this cluttered scene, so pose and collision terms compete",
+            "pose_only": ik_pose_only(w, ev32, torch, n_seeds)}
 
 
 def fused_leg(w, q, n, vtable, args, flush, torch):
