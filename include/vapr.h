@@ -114,7 +114,40 @@ typedef struct {
   int32_t reserved;
   const float* pose;           /* [O][12]: rotation row-major, then centre */
   const float* half_ext;       /* [O][3]: half side lengths (> 0) */
+  const void* grid;            /* NULL, or a broad-phase grid that
+                                  vapr_scene_grid_build made for this scene
+                                  (see there); it changes which cuboids the
+                                  environment loop visits, never a result */
 } vapr_scene;
+
+/* ---- broad-phase grid (scene preprocessing) --------------------------------
+ * A uniform grid of cubic cells over the region where a sphere of radius
+ * <= reach can pass a cuboid's bounding test (centre distance below
+ * r + eta + half diagonal), each cell holding the bitmask of the cuboids
+ * whose test a sphere centred in it can pass.  With scene->grid set, the
+ * collision stage (vapr_collision_cost, vapr_cost_grad, vapr_ik_*,
+ * vapr_surrogate_collision_cost) visits only the cuboids of a sphere's cell,
+ * in cuboid order, with the same bounding test and exact distance: its
+ * outputs are bit-identical to the plain loop over every cuboid.  Each
+ * launch checks on the device that the grid was built for the scene's
+ * current pose and half-extent words (a hash), the same eta and sphere
+ * radii all in [0, reach], and otherwise runs the plain loop, so a stale
+ * grid costs speed, never correctness.  Not used by the multi-problem
+ * launch or the swept cost. */
+#define VAPR_GRID_MAX_CELLS 128
+/* bytes of a grid for n_cuboids cuboids and at most cells_per_axis cells
+ * along each axis (1..VAPR_GRID_MAX_CELLS); 0 when out of range */
+size_t vapr_scene_grid_bytes(int32_t n_cuboids, int32_t cells_per_axis);
+/* Builds the grid of `scene` (scene->grid is ignored) into `grid` (device
+ * memory, 16-byte aligned, grid_bytes >= vapr_scene_grid_bytes), for
+ * spheres of radius <= reach and this eta.  The cell side is the region's
+ * longest extent / cells_per_axis.  Asynchronous on `stream`; the grid
+ * buffer is the caller's and must outlive the launches that use it.  A
+ * scene whose bounding region is not finite, or wider than 1e6 m, gets a
+ * grid marked unusable (the plain loop runs). */
+vapr_status vapr_scene_grid_build(const vapr_scene* scene, float reach, float eta,
+                                  int32_t cells_per_axis, void* grid, size_t grid_bytes,
+                                  void* stream);
 
 /* Cost parameters (reading; the paper delegates them to CuRobo):
  * D_s = sum_o max(0, r_s + eta - d_o(c_s)),

@@ -60,7 +60,8 @@ class vapr_robot(ctypes.Structure):
 
 class vapr_scene(ctypes.Structure):
     _fields_ = [("n_cuboids", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("pose", ctypes.c_void_p), ("half_ext", ctypes.c_void_p)]
+                ("pose", ctypes.c_void_p), ("half_ext", ctypes.c_void_p),
+                ("grid", ctypes.c_void_p)]
 
 
 class vapr_cost_params(ctypes.Structure):
@@ -164,6 +165,9 @@ SIGNATURES = {
     "vapr_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _i64, ctypes.POINTER(vapr_train_params),
                                            _P, ctypes.c_size_t, _P, _P]),
     "vapr_scene_sdf": (ctypes.c_int, [ctypes.POINTER(vapr_scene), _P, _i64, _P, _P]),
+    "vapr_scene_grid_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "vapr_scene_grid_build": (ctypes.c_int, [ctypes.POINTER(vapr_scene), ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_int32, _P, ctypes.c_size_t, _P]),
     "vapr_surrogate_samples": (ctypes.c_int, [ctypes.POINTER(vapr_scene),
                                               ctypes.POINTER(vapr_surrogate_domain), _P, _i64,
                                               ctypes.c_float, ctypes.c_float, _P, _P, _P]),
@@ -271,7 +275,25 @@ class DeviceScene:
             pose, half = np.zeros((1, 12), np.float32), np.zeros((1, 3), np.float32)
         self.pose = torch.as_tensor(pose, device=device)
         self.half_ext = torch.as_tensor(half, device=device)
-        self.c = vapr_scene(n, 0, self.pose.data_ptr(), self.half_ext.data_ptr())
+        self.c = vapr_scene(n, 0, self.pose.data_ptr(), self.half_ext.data_ptr(), None)
+        self.grid = None
+
+    def build_grid(self, reach: float, eta: float, cells: int = 64, stream=None):
+        """Builds the broad-phase grid for spheres of radius <= reach and this
+        eta and attaches it to the scene (``vapr_scene.grid``)."""
+        import torch
+        nb = vapr_scene_grid_bytes(self.c.n_cuboids, cells)
+        if nb == 0:
+            raise ValueError(f"no grid of {cells} cells per axis")
+        buf = torch.empty(nb, dtype=torch.uint8, device=self.pose.device)
+        vapr_scene_grid_build(self, reach, eta, cells, buf, nb, stream)
+        self.grid = buf
+        self.c.grid = buf.data_ptr()
+        return self
+
+    def drop_grid(self):
+        self.grid = None
+        self.c.grid = None
 
 
 def cost_params(p) -> vapr_cost_params:
@@ -493,6 +515,16 @@ def vapr_mlp_train_step(state, u, y, batch, hp, workspace, loss=None, stream=Non
 def vapr_scene_sdf(scene: DeviceScene, pts, n, sdf, stream=None):
     _check(_load().vapr_scene_sdf(ctypes.byref(scene.c), _ptr(pts), n, _ptr(sdf), _stream(stream)),
            "vapr_scene_sdf")
+
+
+def vapr_scene_grid_bytes(n_cuboids: int, cells_per_axis: int) -> int:
+    return int(_load().vapr_scene_grid_bytes(n_cuboids, cells_per_axis))
+
+
+def vapr_scene_grid_build(scene: DeviceScene, reach, eta, cells_per_axis, grid, grid_bytes, stream=None):
+    _check(_load().vapr_scene_grid_build(ctypes.byref(scene.c), float(reach), float(eta), int(cells_per_axis),
+                                         _ptr(grid), int(grid_bytes), _stream(stream)),
+           "vapr_scene_grid_build")
 
 
 def surrogate_domain(lo, hi, pad, margin) -> vapr_surrogate_domain:

@@ -208,6 +208,20 @@ vapr_status check_robot(const vapr_robot* r, RobotArgs* out) {
   return VAPR_OK;
 }
 
+vapr_status check_scene(const vapr_scene* s, SceneArgs* out) {
+  if (!s || s->n_cuboids < 0) return VAPR_ERR_INVALID_ARG;
+  if (s->n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
+  if (s->n_cuboids > 0 && (!s->pose || !s->half_ext)) return VAPR_ERR_INVALID_ARG;
+  if (s->n_cuboids > 0 && (!aligned(s->pose, 16) || !aligned(s->half_ext, 4)))
+    return VAPR_ERR_MISALIGNED;
+  if (s->grid && !aligned(s->grid, 16)) return VAPR_ERR_MISALIGNED;
+  out->O = s->n_cuboids;
+  out->pose = s->pose;
+  out->half = s->half_ext;
+  out->grid = s->grid;
+  return VAPR_OK;
+}
+
 vapr_status check_table(const vapr_format_table* t) {
   if (!t) return VAPR_ERR_INVALID_ARG;
   if (!fmt_ok(t->pos) || !fmt_ok(t->dist) || !fmt_ok(t->grad) || !fmt_ok(t->jgrad) ||
@@ -348,22 +362,15 @@ vapr_status vapr_collision_cost(const vapr_robot* robot, const vapr_scene* scene
   vapr_status st = check_robot(robot, &r);
   if (st != VAPR_OK) return st;
   if ((st = check_table(table)) != VAPR_OK) return st;
-  if (!scene || !params) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids < 0) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
-  if (scene->n_cuboids > 0 && (!scene->pose || !scene->half_ext)) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > 0 && (!aligned(scene->pose, 16) || !aligned(scene->half_ext, 4)))
-    return VAPR_ERR_MISALIGNED;
+  if (!params) return VAPR_ERR_INVALID_ARG;
+  SceneArgs sc;
+  if ((st = check_scene(scene, &sc)) != VAPR_OK) return st;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
   if (n == 0) return VAPR_OK;
   if (!pos_packed) return VAPR_ERR_INVALID_ARG;
   if (!aligned(pos_packed, 16) || (cost && !aligned(cost, 4)) ||
       (dist_packed && !aligned(dist_packed, 16)) || (grad_packed && !aligned(grad_packed, 16)))
     return VAPR_ERR_MISALIGNED;
-  SceneArgs sc;
-  sc.O = scene->n_cuboids;
-  sc.pose = scene->pose;
-  sc.half = scene->half_ext;
   return cuda_status(launch_collision(
       r, sc, *params, packed(pos_packed, 3 * (int64_t)r.S, table->pos), n, cost,
       packed(dist_packed, r.S, table->dist), packed(grad_packed, 3 * (int64_t)r.S, table->grad),
@@ -390,12 +397,9 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
   vapr_status st = check_robot(robot, &r);
   if (st != VAPR_OK) return st;
   if ((st = check_table(table)) != VAPR_OK) return st;
-  if (!scene || !params) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids < 0) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
-  if (scene->n_cuboids > 0 && (!scene->pose || !scene->half_ext)) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > 0 && (!aligned(scene->pose, 16) || !aligned(scene->half_ext, 4)))
-    return VAPR_ERR_MISALIGNED;
+  if (!params) return VAPR_ERR_INVALID_ARG;
+  SceneArgs sc;
+  if ((st = check_scene(scene, &sc)) != VAPR_OK) return st;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
   if (n == 0) return VAPR_OK;
   if (!q || !cost || !jgrad_packed || !workspace) return VAPR_ERR_INVALID_ARG;
@@ -404,10 +408,6 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
       !aligned(jgrad_packed, 16) || (dist_packed && !aligned(dist_packed, 16)) ||
       !aligned(workspace, 256))
     return VAPR_ERR_MISALIGNED;
-  SceneArgs sc;
-  sc.O = scene->n_cuboids;
-  sc.pose = scene->pose;
-  sc.half = scene->half_ext;
   const cudaStream_t s = (cudaStream_t)stream;
   uint8_t* ws = (uint8_t*)workspace;
   Packed pos = packed(ws, 3 * (int64_t)r.S, table->pos);

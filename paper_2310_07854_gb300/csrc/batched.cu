@@ -254,6 +254,7 @@ static vapr_status layout(const vapr_problem* pr, int32_t np, const vapr_format_
     d.sc.O = p.scene.n_cuboids;
     d.sc.pose = p.scene.pose;
     d.sc.half = p.scene.half_ext;
+    d.sc.grid = nullptr;  // every tile visits every cuboid of its problem
     d.eta = p.params.eta;
     d.eta_s = p.params.eta_self;
     d.w_c = p.params.w_coll;

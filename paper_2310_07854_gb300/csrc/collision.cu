@@ -16,6 +16,8 @@
 // (Measured on the 40-cuboid particle workload, this plain scheme issues
 // fewer instructions than per-link candidate lists or a compacted queue of
 // surviving pairs: the bounding test is cheaper than the bookkeeping.)
+// With a broad-phase grid (grid.cuh) each sphere visits only the cuboids
+// listed for its cell, with the same tests in the same order.
 //
 // Determinism: every sphere adds its terms in cuboid order in one register,
 // and a skipped pair would have added exactly zero, so the result of a
@@ -64,6 +66,8 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
   load_scene(a.r, a.sc, a.eta, a.eta_s, sm);
   init_coll_warp(a.r, w, lane);
   __syncthreads();
+  const GridHeader* grid = grid_check(a.sc, a.r, a.eta);  // null: visit every cuboid
+  const uint2* cells = grid ? grid_cells(a.sc) : nullptr;
 
   CollOut out;
   out.dist_words = (int)(a.dist.stride / 4);
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
     collision_config<false, MASKED>(a.r, a.sc.O, rb, sm, w,
                                     reinterpret_cast<const uint32_t*>(a.pos.ptr + c * a.pos.stride),
                                     a.pos.f, a.dist.f, a.grad.f, a.eta, a.w_c, a.w_s, out, lane,
-                                    MASKED ? a.est + c * a.r.S : nullptr, a.margin);
+                                    MASKED ? a.est + c * a.r.S : nullptr, a.margin, grid, cells);
   }
 }
 

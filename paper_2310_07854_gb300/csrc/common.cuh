@@ -23,6 +23,7 @@ struct SceneArgs {
   int O;
   const float* pose;  // [O][12]
   const float* half;  // [O][3]
+  const void* grid = nullptr;  // broad-phase grid (grid.cuh), or null
 };
 
 // A packed tensor: base pointer, row stride in bytes, format.
@@ -37,6 +38,8 @@ DevFmt make_dev_fmt(vapr_format f);
 bool fmt_ok(vapr_format f);
 size_t row_bytes(int64_t row_len, vapr_format f);  // packed row, padded to 16 B
 vapr_status check_robot(const vapr_robot* r, RobotArgs* out);
+// Checks a scene (counts, pointers, alignment) and fills out, grid included.
+vapr_status check_scene(const vapr_scene* s, SceneArgs* out);
 vapr_status check_table(const vapr_format_table* t);
 vapr_status cuda_status(cudaError_t e);           // records the error for vapr_last_cuda_error
 int sm_count();  // SMs of the current device (cached per device)

@@ -248,11 +248,9 @@ static vapr_status check_ik(const vapr_robot* robot, const vapr_scene* scene, co
   vapr_status v = check_robot(robot, r);
   if (v != VAPR_OK) return v;
   if ((v = check_table(table)) != VAPR_OK) return v;
-  if (!scene || !params || !ik || scene->n_cuboids < 0) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
-  if (scene->n_cuboids > 0 && (!scene->pose || !scene->half_ext)) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > 0 && ((uintptr_t)scene->pose % 16 || (uintptr_t)scene->half_ext % 4))
-    return VAPR_ERR_MISALIGNED;
+  if (!params || !ik) return VAPR_ERR_INVALID_ARG;
+  SceneArgs sc;
+  if ((v = check_scene(scene, &sc)) != VAPR_OK) return v;
   if (ik->n_scales < 1 || ik->n_scales > VAPR_IK_MAX_SCALES || ik->history < 1 ||
       ik->history > VAPR_IK_MAX_HISTORY || !(ik->step0 > 0.f) || !ik->q_lo || !ik->q_hi)
     return VAPR_ERR_INVALID_ARG;
@@ -294,9 +292,7 @@ static cudaError_t run_iteration(const RobotArgs& r, const vapr_scene* scene, co
   }
   if (e != cudaSuccess) return e;
   SceneArgs sc;
-  sc.O = scene->n_cuboids;
-  sc.pose = scene->pose;
-  sc.half = scene->half_ext;
+  check_scene(scene, &sc);  // checked by the entry point
   Packed none{nullptr, 0, make_dev_fmt(t->xform)};
   Packed P{w.path, (int64_t)row_bytes(3 * (int64_t)r.S, t->pos), make_dev_fmt(t->pos)};
   Packed G{w.path + w.P_bytes, (int64_t)row_bytes(3 * (int64_t)r.S, t->grad), make_dev_fmt(t->grad)};

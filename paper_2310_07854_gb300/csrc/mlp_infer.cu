@@ -376,15 +376,7 @@ static cudaError_t launch_sdf(const SceneArgs& sc, const float* pts, int64_t n, 
 }
 
 static vapr_status check_scene_args(const vapr_scene* scene, SceneArgs& sc) {
-  if (!scene || scene->n_cuboids < 0) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
-  if (scene->n_cuboids > 0 && (!scene->pose || !scene->half_ext)) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > 0 && ((uintptr_t)scene->pose % 16 || (uintptr_t)scene->half_ext % 4))
-    return VAPR_ERR_MISALIGNED;
-  sc.O = scene->n_cuboids;
-  sc.pose = scene->pose;
-  sc.half = scene->half_ext;
-  return VAPR_OK;
+  return check_scene(scene, &sc);
 }
 
 static vapr_status check_domain(const vapr_surrogate_domain* d) {

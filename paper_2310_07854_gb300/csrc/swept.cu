@@ -217,12 +217,10 @@ extern "C" vapr_status vapr_swept_cost(const vapr_robot* robot, const vapr_scene
   vapr_status v = check_robot(robot, &r);
   if (v != VAPR_OK) return v;
   if ((v = check_table(table)) != VAPR_OK) return v;
-  if (!scene || !params) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids < 0) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
-  if (scene->n_cuboids > 0 && (!scene->pose || !scene->half_ext)) return VAPR_ERR_INVALID_ARG;
-  if (scene->n_cuboids > 0 && ((uintptr_t)scene->pose % 16 || (uintptr_t)scene->half_ext % 4))
-    return VAPR_ERR_MISALIGNED;
+  if (!params) return VAPR_ERR_INVALID_ARG;
+  SceneArgs sc;
+  if ((v = check_scene(scene, &sc)) != VAPR_OK) return v;
+  sc.grid = nullptr;  // the swept loop visits every cuboid
   if (n < 0 || horizon < 1 || samples < 1) return VAPR_ERR_INVALID_ARG;
   if (samples > VAPR_MAX_SWEPT_SAMPLES) return VAPR_ERR_TOO_LARGE;
   if (n % horizon) return VAPR_ERR_INVALID_ARG;
@@ -233,9 +231,7 @@ extern "C" vapr_status vapr_swept_cost(const vapr_robot* robot, const vapr_scene
     return VAPR_ERR_MISALIGNED;
   SweptArgs a;
   a.r = r;
-  a.sc.O = scene->n_cuboids;
-  a.sc.pose = scene->pose;
-  a.sc.half = scene->half_ext;
+  a.sc = sc;
   a.eta = params->eta;
   a.w_c = params->w_coll;
   a.pos = Packed{(uint8_t*)pos_packed, (int64_t)row_bytes(3 * (int64_t)r.S, table->pos), make_dev_fmt(table->pos)};

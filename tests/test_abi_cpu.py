@@ -213,3 +213,39 @@ def test_swept_argument_checks():
     assert call(64, 32, 4, pos=4104) == 3
     assert lib.vapr_swept_cost(ctypes.byref(robot), None, ctypes.byref(params), 4096, 64, 32, 4,
                                ctypes.byref(t), None, None, None, None) == 1
+
+
+def test_scene_grid_bytes_and_checks():
+    lib = B.lib()
+    byref = ctypes.byref
+    # header + cells^3 x (2 words per 64 cuboids) x 4 bytes
+    assert B.vapr_scene_grid_bytes(40, 48) == 128 + 48 ** 3 * 2 * 4
+    assert B.vapr_scene_grid_bytes(0, 8) == 128 + 8 ** 3 * 2 * 4
+    assert B.vapr_scene_grid_bytes(64, 8) == 128 + 8 ** 3 * 2 * 4
+    assert B.vapr_scene_grid_bytes(65, 8) == 128 + 8 ** 3 * 4 * 4
+    assert B.vapr_scene_grid_bytes(B.MAX_CUBOIDS, 128) == 128 + 128 ** 3 * 32 * 4
+    for bad in ((-1, 8), (B.MAX_CUBOIDS + 1, 8), (40, 0), (40, 129)):
+        assert B.vapr_scene_grid_bytes(*bad) == 0, bad
+    sc = B.vapr_scene(8, 0, 256, 256)
+    nb = B.vapr_scene_grid_bytes(8, 16)
+    build = lambda scene, reach=0.1, eta=0.02, cells=16, grid=4096, nbytes=nb: lib.vapr_scene_grid_build(
+        scene, reach, eta, cells, grid, nbytes, None)
+    assert build(None) == 1
+    assert build(byref(B.vapr_scene(B.MAX_CUBOIDS + 1, 0, 256, 256))) == 6   # too large
+    assert build(byref(B.vapr_scene(8, 0, 260, 256))) == 3                    # pose misaligned
+    assert build(byref(sc), reach=-0.1) == 1
+    assert build(byref(sc), reach=float("nan")) == 1
+    assert build(byref(sc), reach=float("inf")) == 1
+    assert build(byref(sc), eta=float("nan")) == 1
+    assert build(byref(sc), cells=0) == 1
+    assert build(byref(sc), cells=129) == 1
+    assert build(byref(sc), grid=None) == 1
+    assert build(byref(sc), grid=4104) == 3                                   # grid misaligned
+    assert build(byref(sc), nbytes=nb - 1) == 1
+    # a scene whose grid pointer is misaligned is rejected by the collision stage
+    r = _robot_struct()
+    t = B.to_c_table(F.FP32_TABLE)
+    p = B.vapr_cost_params(0.02, 0.01, 1.0, 1.0)
+    sc_bad = B.vapr_scene(8, 0, 256, 256, 4104)
+    assert lib.vapr_collision_cost(byref(r), byref(sc_bad), byref(p), 256, 4, byref(t),
+                                   None, None, None, None) == 3
