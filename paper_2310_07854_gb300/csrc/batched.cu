@@ -73,19 +73,25 @@ struct PlanHost {
 static_assert(sizeof(PlanHost) <= sizeof(vapr_batch_plan), "plan handle too small");
 constexpr uint64_t PLAN_MAGIC = 0x5641505242415443ull;
 
+// The self-table scratch lies over the warps' working sets, sU and sQ (not
+// live while a problem's tables are built).
 __host__ __device__ inline void carve_batch(Bump& b, const BatchArgs& a, RobotSm& rb, SceneSm& sm,
                                             CollWarp& w_mine, int mine, float4*& sU, float*& sQ,
-                                            int*& sItem) {
+                                            int*& sItem, SelfScratch& scratch) {
   carve_robot(b, a.maxJ, a.maxS, rb);
-  carve_scene(b, a.maxO, a.maxNP, sm);
+  carve_scene(b, a.maxO, a.maxNP, cluster_bound(a.maxS, a.maxJ), sm);
+  Bump t(b.base);
+  t.off = b.bytes();
   for (int w = 0; w < BT_WARPS; ++w) {
-    CollWarp t;
-    carve_coll_warp(b, a.maxS, a.maxJ, t);
-    if (w == mine) w_mine = t;
+    CollWarp cw;
+    carve_coll_warp(b, a.maxS, a.maxJ, cw);
+    if (w == mine) w_mine = cw;
   }
   const int tstride = (3 * a.maxJ) | 1, kstride = (2 * a.maxJ) | 1;
   sU = b.take<float4>((size_t)a.tile * (tstride > kstride ? tstride : kstride));  // T, then K
   sQ = b.take<float>((size_t)a.tile * a.maxJ);
+  carve_self_scratch(t, a.maxNP, cluster_bound(a.maxS, a.maxJ), scratch);
+  if (t.off > b.off) b.off = t.off;
   sItem = b.take<int>(4);
 }
 
@@ -105,7 +111,8 @@ __global__ void __launch_bounds__(BT_BLOCK) batched_kernel(BatchArgs a) {
   float4* sU;
   float* sQ;
   int* sItem;
-  carve_batch(b, a, rb, sm, w, warp, sU, sQ, sItem);
+  SelfScratch self_scr;
+  carve_batch(b, a, rb, sm, w, warp, sU, sQ, sItem, self_scr);
   uint8_t* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_block;
   int cur = -1;
   for (;;) {
@@ -144,6 +151,8 @@ __global__ void __launch_bounds__(BT_BLOCK) batched_kernel(BatchArgs a) {
       load_robot(P.r, rb);
       load_scene(P.r, P.sc, P.eta, P.eta_s, sm);
       __syncthreads();
+      load_clusters(J, S, rb);
+      load_self(P.r, rb, sm, self_scr, P.eta_s);
       init_coll_warp(P.r, w, lane);
       cur = it.problem;
     }
@@ -298,7 +307,8 @@ static vapr_status layout(const vapr_problem* pr, int32_t np, const vapr_format_
   float4* sU;
   float* sQ;
   int* sItem;
-  carve_batch(b, a, rb, sm, w, 0, sU, sQ, sItem);
+  SelfScratch scratch;
+  carve_batch(b, a, rb, sm, w, 0, sU, sQ, sItem, scratch);
   L.smem = b.bytes();
   L.kern = batched_for(a.fG.kind);
   const int per_sm = blocks_per_sm((const void*)L.kern, BT_BLOCK, L.smem);

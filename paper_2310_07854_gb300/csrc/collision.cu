@@ -19,11 +19,17 @@
 // With a broad-phase grid (grid.cuh) each sphere visits only the cuboids
 // listed for its cell, with the same tests in the same order.
 //
+// Self pairs: the block groups the pair table by cluster pair (runs of up to
+// three spheres of one link, load_self); per configuration, cluster pairs
+// whose bounding spheres are apart are skipped and the pairs of the others
+// tested in table order (self_pairs in stages.cuh).
+//
 // Determinism: every sphere adds its terms in cuboid order in one register,
 // and a skipped pair would have added exactly zero, so the result of a
 // configuration does not depend on the batch it is in or on which pairs the
-// bounding test lets through.  Active self pairs are applied one lane at a
-// time in pair order.
+// bounding test lets through.  Active self pairs are applied sphere-major in
+// table order; which lane sums a pair's penetration follows from the
+// configuration's own kept cluster pairs.
 #include "stages.cuh"
 
 namespace vapr {
@@ -42,15 +48,21 @@ struct CollArgs {
 };
 
 // Carves the block's tables and every warp's working set; keeps warp `mine`'s.
+// The self-table scratch lies over the warps' working sets (built first).
 __host__ __device__ inline void carve_coll(Bump& b, const RobotArgs& r, int O, RobotSm& rb,
-                                           SceneSm& sm, CollWarp& w_mine, int mine) {
+                                           SceneSm& sm, CollWarp& w_mine, int mine,
+                                           SelfScratch& scratch) {
   carve_robot(b, r.J, r.S, rb);
-  carve_scene(b, O, r.NP, sm);
+  carve_scene(b, O, r.NP, cluster_bound(r.S, r.J), sm);
+  Bump t(b.base);
+  t.off = b.bytes();
   for (int w = 0; w < COLL_WARPS; ++w) {
-    CollWarp t;
-    carve_coll_warp(b, r.S, r.J, t);
-    if (w == mine) w_mine = t;
+    CollWarp cw;
+    carve_coll_warp(b, r.S, r.J, cw);
+    if (w == mine) w_mine = cw;
   }
+  carve_self_scratch(t, r.NP, cluster_bound(r.S, r.J), scratch);
+  if (t.off > b.off) b.off = t.off;
 }
 
 template <bool MASKED>
@@ -61,9 +73,13 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
   RobotSm rb;
   SceneSm sm;
   CollWarp w;
-  carve_coll(b, a.r, a.sc.O, rb, sm, w, wid);
+  SelfScratch scratch;
+  carve_coll(b, a.r, a.sc.O, rb, sm, w, wid, scratch);
   load_robot(a.r, rb);
   load_scene(a.r, a.sc, a.eta, a.eta_s, sm);
+  __syncthreads();
+  load_clusters(a.r.J, a.r.S, rb);
+  load_self(a.r, rb, sm, scratch, a.eta_s);
   init_coll_warp(a.r, w, lane);
   __syncthreads();
   const GridHeader* grid = grid_check(a.sc, a.r, a.eta);  // null: visit every cuboid
@@ -118,7 +134,8 @@ cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc, const vapr
   RobotSm rb;
   SceneSm sm;
   CollWarp w;
-  carve_coll(b, r, sc.O, rb, sm, w, 0);
+  SelfScratch scratch;
+  carve_coll(b, r, sc.O, rb, sm, w, 0, scratch);
   const size_t smem = b.bytes();
   const void* fn = est ? (const void*)collision_kernel<true> : (const void*)collision_kernel<false>;
   const int per_sm = blocks_per_sm(fn, COLL_WARPS * 32, smem);

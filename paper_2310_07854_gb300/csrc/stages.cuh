@@ -39,12 +39,20 @@ struct Bump {
 };
 
 // ------------------------------------------------------------ robot tables
+// Self-collision clusters: runs of at most CL consecutive spheres of one
+// link (in the link-grouped order), at most cluster_bound(S, J) of them.
+constexpr int CL = 3;
+__host__ __device__ constexpr int cluster_bound(int S, int J) { return (S + (CL - 1) * J) / CL + 1; }
+
 struct RobotSm {
-  float4* F;    // [3J] rows of F_j: (R_d0, R_d1, R_d2, t_d)
-  float4* sph;  // [S] (p, r)
-  int* link0;   // [S] 0-based link, clamped into range
-  int* order;   // [S] spheres grouped by link (stable)
-  int* start;   // [J+1] first slot of each link in order
+  float4* F;      // [3J] rows of F_j: (R_d0, R_d1, R_d2, t_d)
+  float4* sph;    // [S] (p, r)
+  int* link0;     // [S] 0-based link, clamped into range
+  int* order;     // [S] spheres grouped by link (stable)
+  int* start;     // [J+1] first slot of each link in order
+  int* cl_start;  // [NC+1] cluster c = spheres order[cl_start[c] .. cl_start[c+1])
+  int* cl_of;     // [S] cluster of each sphere
+  int* n_cl;      // [1] NC
 };
 
 __host__ __device__ inline void carve_robot(Bump& b, int J, int S, RobotSm& r) {
@@ -53,9 +61,14 @@ __host__ __device__ inline void carve_robot(Bump& b, int J, int S, RobotSm& r) {
   r.link0 = b.take<int>(S);
   r.order = b.take<int>(S);
   r.start = b.take<int>(J + 1);
+  r.cl_start = b.take<int>(cluster_bound(S, J) + 1);
+  r.cl_of = b.take<int>(S);
+  r.n_cl = b.take<int>(1);
 }
 
-// Block-cooperative; the caller synchronises the block afterwards.
+// Block-cooperative (every thread calls it); the caller synchronises the
+// block afterwards.  The spheres are sorted by link (stably) in parallel:
+// each sphere's slot counts the spheres before it in (link, index) order.
 __device__ inline void load_robot(const RobotArgs& a, const RobotSm& r) {
   const int J = a.J, S = a.S;
   for (int i = threadIdx.x; i < 3 * J; i += blockDim.x) {
@@ -67,14 +80,46 @@ __device__ inline void load_robot(const RobotArgs& a, const RobotSm& r) {
     r.sph[s] = reinterpret_cast<const float4*>(a.sphere_local)[s];
     r.link0[s] = clampi(a.sphere_link[s], 1, J) - 1;
   }
-  if (threadIdx.x == 0) {  // stable counting sort of the spheres by link
-    for (int j = 0; j <= J; ++j) r.start[j] = 0;
-    for (int s = 0; s < S; ++s) ++r.start[clampi(a.sphere_link[s], 1, J)];
-    for (int j = 1; j <= J; ++j) r.start[j] += r.start[j - 1];
-    for (int s = S - 1; s >= 0; --s) r.order[--r.start[clampi(a.sphere_link[s], 1, J)]] = s;
-    for (int j = 0; j < J; ++j) r.start[j] = r.start[j + 1];
-    r.start[J] = S;
+  __syncthreads();
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const int l = r.link0[s];
+    int slot = 0;
+    for (int t = 0; t < S; ++t) {
+      const int lt = r.link0[t];
+      slot += (lt < l) || (lt == l && t < s);
+    }
+    r.order[slot] = s;
   }
+  for (int j = threadIdx.x; j <= J; j += blockDim.x) {  // first slot of each link
+    int c = 0;
+    for (int t = 0; t < S; ++t) c += r.link0[t] < j;
+    r.start[j] = c;
+  }
+}
+
+// Block-cooperative, after load_robot and a block synchronisation: the
+// self-collision clusters (runs of up to CL spheres of one link in the
+// link-sorted order).  Ends with the block synchronised.
+__device__ inline void load_clusters(int J, int S, const RobotSm& r) {
+  auto clusters_before = [&](int j) {
+    int c = 0;
+    for (int i = 0; i < j; ++i) c += (r.start[i + 1] - r.start[i] + CL - 1) / CL;
+    return c;
+  };
+  for (int j = threadIdx.x; j < J; j += blockDim.x) {
+    const int c0 = clusters_before(j), nj = r.start[j + 1] - r.start[j];
+    for (int c = 0; c * CL < nj; ++c) r.cl_start[c0 + c] = r.start[j] + c * CL;
+    if (j == J - 1) {
+      const int nc = c0 + (nj + CL - 1) / CL;
+      r.cl_start[nc] = S;
+      r.n_cl[0] = nc;
+    }
+  }
+  for (int k = threadIdx.x; k < S; k += blockDim.x) {
+    const int s = r.order[k], j = r.link0[s];
+    r.cl_of[s] = clusters_before(j) + (k - r.start[j]) / CL;
+  }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------ FK (thread)
@@ -143,15 +188,46 @@ struct SceneSm {
   float4* cubA;  // [O][3]: (column k of R, t_k), k = 0..2
   float4* cubH;  // [O]: (half extents, unused)
   float4* cubC;  // [O]: (centre, bounding radius + eta + SLACK)
-  uint2* pairs;  // [NP]: (i | j << 16, bits of r_i + r_j + eta_s)
+  // self pairs, grouped by cluster pair (load_self)
+  uint2* pairs;         // [NP]: (i | j << 16, bits of r_i + r_j + eta_s), cluster-pair major
+  uint16_t* cp;         // [NG]: cluster pair a | b << 8 (a <= b), in increasing a * NC + b
+  uint16_t* cp_start;   // [NG+1]: its pairs are pairs[cp_start[g] .. cp_start[g+1])
+  int* self_meta;       // [2]: NG, bits of eta_s
 };
 
-__host__ __device__ inline void carve_scene(Bump& b, int O, int NP, SceneSm& s) {
+__host__ __device__ inline int pair_groups_bound(int NP, int NCB) {
+  return NP < NCB * NCB ? NP : NCB * NCB;
+}
+
+// NCB: cluster_bound of the largest robot the tables serve.
+__host__ __device__ inline void carve_scene(Bump& b, int O, int NP, int NCB, SceneSm& s) {
   s.cubA = b.take<float4>(3 * O);
   s.cubH = b.take<float4>(O);
   s.cubC = b.take<float4>(O);
+  const int NG = pair_groups_bound(NP, NCB);
   s.pairs = b.take<uint2>(NP);
+  s.cp = b.take<uint16_t>(NG);
+  s.cp_start = b.take<uint16_t>(NG + 1);
+  s.self_meta = b.take<int>(2);
 }
+
+// Scratch of load_self; callers lay it over buffers that are not live
+// while the tables are built (the warps' working sets).
+struct SelfScratch {
+  uint32_t* word;      // [NP] per pair: i | j << 7 | (key, then cluster pair) << 14
+  int* cursor;         // [NG] pair counts, then fill cursors
+  uint16_t* g_of_key;  // [NC^2]
+  uint32_t* keymap;    // [NC^2 / 32] keys that occur
+};
+
+__host__ __device__ inline void carve_self_scratch(Bump& b, int NP, int NCB, SelfScratch& t) {
+  const int keys = NP > 0 ? NCB * NCB : 0;
+  t.word = b.take<uint32_t>(NP);
+  t.cursor = b.take<int>(pair_groups_bound(NP, NCB));
+  t.g_of_key = b.take<uint16_t>(keys);
+  t.keymap = b.take<uint32_t>((keys + 31) / 32);
+}
+static_assert(VAPR_MAX_SPHERES <= 128, "sphere indices are packed in 7 bits");
 
 __device__ inline void load_scene(const RobotArgs& r, const SceneArgs& sc, float eta, float eta_s,
                                   const SceneSm& m) {
@@ -165,28 +241,118 @@ __device__ inline void load_scene(const RobotArgs& r, const SceneArgs& sc, float
     m.cubH[o] = make_float4(hx, hy, hz, 0.f);
     m.cubC[o] = make_float4(p[9], p[10], p[11], sqrtf(hx * hx + hy * hy + hz * hz) + eta + SLACK);
   }
-  for (int p = threadIdx.x; p < r.NP; p += blockDim.x) {
-    const int i = clampi(r.pairs[2 * p], 0, S - 1), j = clampi(r.pairs[2 * p + 1], 0, S - 1);
-    m.pairs[p] = make_uint2((uint32_t)i | ((uint32_t)j << 16),
-                            __float_as_uint(r.sphere_local[4 * i + 3] + r.sphere_local[4 * j + 3] +
-                                            eta_s));
+  (void)S;
+  (void)eta_s;
+}
+
+// Inclusive warp scan of v.
+__device__ __forceinline__ int warp_scan(int v, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int t = __shfl_up_sync(FULL_MASK, v, off);
+    if (lane >= off) v += t;
   }
+  return v;
+}
+
+// Block-cooperative (all threads, block converged; load_robot's and
+// load_clusters' tables complete): the self-pair table grouped by cluster
+// pair.  Cluster pairs are numbered in increasing key a * NC + b and the
+// pairs within one keep the robot's order (a stable counting sort, so the
+// table does not depend on thread timing).  The robot's pair list is read
+// once, in parallel; the one serial pass (the scatter, a warp over 32 pairs
+// at a time) touches shared memory only.  Ends with the block synchronised.
+__device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const SceneSm& m,
+                                 const SelfScratch& t, float eta_s) {
+  const int NP = r.NP, NC = rb.n_cl[0], keys = NC * NC, kw = (keys + 31) / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < kw; k += blockDim.x) t.keymap[k] = 0u;
+  __syncthreads();
+  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+    const int i = clampi(r.pairs[2 * p], 0, r.S - 1), j = clampi(r.pairs[2 * p + 1], 0, r.S - 1);
+    const int a = rb.cl_of[i], b = rb.cl_of[j];
+    const int key = a <= b ? a * NC + b : b * NC + a;
+    t.word[p] = (uint32_t)i | ((uint32_t)j << 7) | ((uint32_t)key << 14);
+    atomicOr(&t.keymap[key >> 5], 1u << (key & 31));
+  }
+  __syncthreads();
+  if (warp == 0) {  // number the keys that occur, in increasing order
+    int base = 0;
+    for (int k0 = 0; k0 < kw; k0 += 32) {
+      const uint32_t bits = k0 + lane < kw ? t.keymap[k0 + lane] : 0u;
+      const int incl = warp_scan(__popc(bits), lane);
+      int g = base + incl - __popc(bits);
+      for (uint32_t bb = bits; bb; bb &= bb - 1u) {
+        const int key = 32 * (k0 + lane) + __ffs(bb) - 1;
+        t.g_of_key[key] = (uint16_t)g;
+        m.cp[g] = (uint16_t)((key / NC) | ((key % NC) << 8));
+        t.cursor[g] = 0;
+        ++g;
+      }
+      base += __shfl_sync(FULL_MASK, incl, 31);
+    }
+    if (lane == 0) {
+      m.self_meta[0] = base;
+      m.self_meta[1] = (int)__float_as_uint(eta_s);
+    }
+  }
+  __syncthreads();
+  const int NG = m.self_meta[0];
+  for (int p = threadIdx.x; p < NP; p += blockDim.x) {  // pairs per cluster pair
+    const uint32_t wd = t.word[p];
+    const int g = t.g_of_key[wd >> 14];
+    t.word[p] = (wd & 0x3fffu) | ((uint32_t)g << 14);
+    atomicAdd(&t.cursor[g], 1);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int base = 0;  // exclusive scan of the counts: group starts, and the fill cursors
+    for (int g0 = 0; g0 < NG; g0 += 32) {
+      const int g = g0 + lane;
+      const int c = g < NG ? t.cursor[g] : 0;
+      const int incl = warp_scan(c, lane);
+      if (g < NG) {
+        m.cp_start[g] = (uint16_t)(base + incl - c);
+        t.cursor[g] = base + incl - c;
+      }
+      base += __shfl_sync(FULL_MASK, incl, 31);
+    }
+    if (lane == 0) m.cp_start[NG] = (uint16_t)base;
+    __syncwarp();
+    for (int p0 = 0; p0 < NP; p0 += 32) {  // stable scatter, in pair order
+      const int p = p0 + lane;
+      const uint32_t wd = p < NP ? t.word[p] : 0u;
+      const int g = p < NP ? (int)(wd >> 14) : -1 - lane;
+      const unsigned same = __match_any_sync(FULL_MASK, g);
+      if (p < NP) {
+        const int i = (int)(wd & 0x7fu), j = (int)((wd >> 7) & 0x7fu);
+        m.pairs[t.cursor[g] + __popc(same & ((1u << lane) - 1u))] =
+            make_uint2((uint32_t)i | ((uint32_t)j << 16),
+                       __float_as_uint(rb.sph[i].w + rb.sph[j].w + eta_s));
+      }
+      __syncwarp();
+      if (p < NP && lane == __ffs(same) - 1) t.cursor[g] += __popc(same);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
 }
 
 // One warp's working set for one configuration.
 constexpr int ACT_CAP = 64;  // warp list of active self pairs awaiting their gradient update
 
 struct CollWarp {
-  float4* P;    // [S] (x, y, z, r)
-  float4* acc;  // [S] (D, gx, gy, gz)
-  float4* act;  // [ACT_CAP] active self pairs: (bits of i | j << 16, u) with u = w_s (c_i - c_j)/|c_i - c_j|
+  float4* P;       // [S] (x, y, z, r)
+  float4* acc;     // [S] (D, gx, gy, gz)
+  float4* act;     // [ACT_CAP] active self pairs: (bits of i | j << 16, u) with u = w_s (c_i - c_j)/|c_i - c_j|
+  float4* cls;     // [NC] cluster bounding spheres of this configuration (centre, radius)
 };
 
 __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp& w) {
-  (void)J;
   w.P = b.take<float4>(S);
   w.acc = b.take<float4>(S);
   w.act = b.take<float4>(ACT_CAP);
+  w.cls = b.take<float4>(cluster_bound(S, J));
 }
 
 // Applies the listed active self pairs to acc, sphere-major: each lane takes
@@ -334,6 +500,111 @@ __device__ __forceinline__ void env_bits(const SceneSm& m, int obase, unsigned l
   }
 }
 
+// Self-collision of one configuration (P in w.P, acc receiving gradients):
+// returns this lane's share of the penetration sum.
+//
+// Each cluster's bounding sphere comes from the decoded centres: the
+// centroid, radius rho = the largest |c_s - centroid| + r_s.  A cluster
+// pair (a, b) whose spheres are apart by d_ab - rho_a - rho_b >= eta_s (+ a
+// rounding margin) holds no pair with |c_i - c_j| < r_i + r_j + eta_s, since
+// |c_i - c_j| >= d_ab - (rho_a - r_i) - (rho_b - r_j): its pairs are skipped.
+// (A NaN anywhere keeps the cluster pair.)  The kept cluster pairs of each
+// 32 are expanded into their pairs through a warp prefix sum of their pair
+// counts (lane t of a chunk finds its cluster pair by binary search), and
+// the pairs are tested in table order; active pairs are listed and applied
+// sphere-major in that order.
+__device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m, const CollWarp& w,
+                                            int S, float w_s, int lane) {
+  const int NC = rb.n_cl[0], NG = m.self_meta[0];
+  const float eta_s = __int_as_float(m.self_meta[1]);
+  for (int c = lane; c < NC; c += 32) {
+    const int k0 = rb.cl_start[c], k1 = rb.cl_start[c + 1];
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int k = k0; k < k1; ++k) {
+      const float4 p = w.P[rb.order[k]];
+      sx += p.x;
+      sy += p.y;
+      sz += p.z;
+    }
+    const float inv = __fdividef(1.f, (float)(k1 - k0));
+    const float cx = sx * inv, cy = sy * inv, cz = sz * inv;
+    float rho = 0.f;
+    for (int k = k0; k < k1; ++k) {
+      const float4 p = w.P[rb.order[k]];
+      const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
+      const float e2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      // |c_s - centroid| from the hardware reciprocal square root, rounded up
+      rho = fmaxf(rho, fmaf(e2 > 0.f ? e2 * rsqrtf(e2) : 0.f, 1.000001f, p.w));
+    }
+    w.cls[c] = make_float4(cx, cy, cz, rho);
+  }
+  __syncwarp();
+  float selfsum = 0.f;
+  int n_act = 0;
+  for (int g0 = 0; g0 < NG; g0 += 32) {
+    const int g = g0 + lane;
+    int cnt = 0, st = 0;
+    if (g < NG) {
+      const uint32_t ab = m.cp[g];
+      const float4 A = w.cls[ab & 0xffu], B = w.cls[ab >> 8];
+      const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float mag = fabsf(A.x) + fabsf(A.y) + fabsf(A.z) + fabsf(B.x) + fabsf(B.y) + fabsf(B.z);
+      const float rhs = A.w + B.w + eta_s + fmaf(4e-6f, mag + A.w + B.w, 1e-4f);
+      if (!(rhs <= 0.f || d2 >= rhs * rhs)) {  // kept
+        st = m.cp_start[g];
+        cnt = m.cp_start[g + 1] - st;
+      }
+    }
+    const int incl = warp_scan(cnt, lane), excl = incl - cnt;
+    const int total = __shfl_sync(FULL_MASK, incl, 31);
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int v = t0 + lane;
+      int owner = 0;  // first lane whose inclusive count exceeds v
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(FULL_MASK, incl, owner + step - 1) <= v) owner += step;
+      const int pst = __shfl_sync(FULL_MASK, st, owner), pex = __shfl_sync(FULL_MASK, excl, owner);
+      bool act = false;
+      float pen = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+      int i = 0, j = 0;
+      if (v < total) {
+        const uint2 pr = m.pairs[pst + v - pex];
+        i = (int)(pr.x & 0xffffu);
+        j = (int)(pr.x >> 16);
+        const float4 ci = w.P[i], cj = w.P[j];
+        const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float thr = __uint_as_float(pr.y);
+        if (d2 < thr * thr) {
+          const float rs = d2 > 0.f ? rsqrtf(d2) : 0.f;
+          pen = thr - d2 * rs;
+          act = pen > 0.f;
+          const float inv = w_s * rs;  // 0 at zero distance: no gradient
+          ux = dx * inv;
+          uy = dy * inv;
+          uz = dz * inv;
+        }
+      }
+      const unsigned am = __ballot_sync(FULL_MASK, act);
+      if (act) {  // list the active pair (table order = lane order within the chunk)
+        selfsum += pen;
+        w.act[n_act + __popc(am & ((1u << lane) - 1u))] =
+            make_float4(__uint_as_float((uint32_t)i | ((uint32_t)j << 16)), ux, uy, uz);
+      }
+      n_act += __popc(am);
+      if (n_act > ACT_CAP - 32) {  // the next chunk might not fit: apply what is listed
+        __syncwarp();
+        apply_self_pairs(w, S, n_act, lane);
+        n_act = 0;
+      }
+    }
+  }
+  __syncwarp();
+  if (n_act > 0) apply_self_pairs(w, S, n_act, lane);
+  return selfsum;
+}
+
 // Environment terms of sphere p (when v) over the candidates of its grid cell.
 __device__ __forceinline__ void env_grid(const SceneSm& m, const GridHeader& g, const uint2* cells,
                                          bool v, const float4& p, float eta, float w_c, float4& acc) {
@@ -364,8 +635,7 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
                                                  float margin = 0.f,
                                                  const GridHeader* grid = nullptr,
                                                  const uint2* cells = nullptr) {
-  (void)rb;
-  const int S = r.S, NP = r.NP;
+  const int S = r.S;
   // ---- 1. sphere centres (one word per lane)
   load_centres<COHERENT>(prow, fP, S, w.P, lane);
   __syncwarp();
@@ -405,48 +675,9 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
     if (sb < S) w.acc[sb] = accb;
   }
   __syncwarp();
-  // ---- 4. self-collision over the pair list; active pairs are listed and
-  //      their gradients applied sphere-major in pair order
-  float selfsum = 0.f;
-  int n_act = 0;
-  for (int pb = 0; pb < NP; pb += 32) {
-    const int p = pb + lane;
-    bool act = false;
-    float pen = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-    int i = 0, j = 0;
-    if (p < NP) {
-      const uint2 pr = m.pairs[p];
-      i = (int)(pr.x & 0xffffu);
-      j = (int)(pr.x >> 16);
-      const float4 ci = w.P[i], cj = w.P[j];
-      const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
-      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float thr = __uint_as_float(pr.y);
-      if (d2 < thr * thr) {
-        const float rs = d2 > 0.f ? rsqrtf(d2) : 0.f;
-        pen = thr - d2 * rs;
-        act = pen > 0.f;
-        const float inv = w_s * rs;  // 0 at zero distance: no gradient
-        ux = dx * inv;
-        uy = dy * inv;
-        uz = dz * inv;
-      }
-    }
-    const unsigned am = __ballot_sync(FULL_MASK, act);
-    if (act) {  // list the active pair (pair order = lane order within the chunk)
-      selfsum += pen;
-      w.act[n_act + __popc(am & ((1u << lane) - 1u))] =
-          make_float4(__uint_as_float((uint32_t)i | ((uint32_t)j << 16)), ux, uy, uz);
-    }
-    n_act += __popc(am);
-    if (n_act > ACT_CAP - 32) {  // the next chunk might not fit: apply what is listed
-      __syncwarp();
-      apply_self_pairs(w, S, n_act, lane);
-      n_act = 0;
-    }
-  }
-  __syncwarp();
-  if (n_act > 0) apply_self_pairs(w, S, n_act, lane);
+  // ---- 4. self-collision: cluster bounding spheres, then the pairs of the
+  //      cluster pairs whose spheres can touch (self_pairs)
+  const float selfsum = self_pairs(rb, m, w, S, w_s, lane);
   // ---- 5. cost and packed outputs, then reset acc
   coll_outputs(w, S, fD, fG, w_c, w_s * selfsum, out, lane);
 }

@@ -38,7 +38,7 @@ struct SweptArgs {
 __host__ __device__ inline void carve_swept(Bump& b, const RobotArgs& r, int O, RobotSm& rb, SceneSm& sm,
                                             CollWarp& w_mine, float4*& Pn, float4*& Pp, int mine) {
   carve_robot(b, r.J, r.S, rb);
-  carve_scene(b, O, 0, sm);
+  carve_scene(b, O, 0, 0, sm);
   for (int w = 0; w < SW_WARPS; ++w) {
     CollWarp t;
     carve_coll_warp(b, r.S, r.J, t);
