@@ -218,6 +218,7 @@ struct SelfScratch {
   int* cursor;         // [NG] pair counts, then fill cursors
   uint16_t* g_of_key;  // [NC^2]
   uint32_t* keymap;    // [NC^2 / 32] keys that occur
+  int* keybase;        // [NC^2 / 32] keys that occur in earlier keymap words
 };
 
 __host__ __device__ inline void carve_self_scratch(Bump& b, int NP, int NCB, SelfScratch& t) {
@@ -226,6 +227,7 @@ __host__ __device__ inline void carve_self_scratch(Bump& b, int NP, int NCB, Sel
   t.cursor = b.take<int>(pair_groups_bound(NP, NCB));
   t.g_of_key = b.take<uint16_t>(keys);
   t.keymap = b.take<uint32_t>((keys + 31) / 32);
+  t.keybase = b.take<int>((keys + 31) / 32);
 }
 static_assert(VAPR_MAX_SPHERES <= 128, "sphere indices are packed in 7 bits");
 
@@ -276,24 +278,28 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
     atomicOr(&t.keymap[key >> 5], 1u << (key & 31));
   }
   __syncthreads();
-  if (warp == 0) {  // number the keys that occur, in increasing order
+  if (warp == 0) {  // keys occurring in earlier words
     int base = 0;
     for (int k0 = 0; k0 < kw; k0 += 32) {
-      const uint32_t bits = k0 + lane < kw ? t.keymap[k0 + lane] : 0u;
-      const int incl = warp_scan(__popc(bits), lane);
-      int g = base + incl - __popc(bits);
-      for (uint32_t bb = bits; bb; bb &= bb - 1u) {
-        const int key = 32 * (k0 + lane) + __ffs(bb) - 1;
-        t.g_of_key[key] = (uint16_t)g;
-        m.cp[g] = (uint16_t)((key / NC) | ((key % NC) << 8));
-        t.cursor[g] = 0;
-        ++g;
-      }
+      const int c = k0 + lane < kw ? __popc(t.keymap[k0 + lane]) : 0;
+      const int incl = warp_scan(c, lane);
+      if (k0 + lane < kw) t.keybase[k0 + lane] = base + incl - c;
       base += __shfl_sync(FULL_MASK, incl, 31);
     }
     if (lane == 0) {
       m.self_meta[0] = base;
       m.self_meta[1] = (int)__float_as_uint(eta_s);
+    }
+  }
+  __syncthreads();
+  for (int key = threadIdx.x; key < keys; key += blockDim.x) {  // number the keys that occur
+    const uint32_t bits = t.keymap[key >> 5], bit = 1u << (key & 31);
+    if (bits & bit) {
+      const int g = t.keybase[key >> 5] + __popc(bits & (bit - 1u));
+      const int a = key / NC;
+      t.g_of_key[key] = (uint16_t)g;
+      m.cp[g] = (uint16_t)(a | ((key - a * NC) << 8));
+      t.cursor[g] = 0;
     }
   }
   __syncthreads();
