@@ -225,7 +225,7 @@ def time_steps(ev, q, n, steps, warmup, flush_buf, torch):
 
 KERNEL_SOURCES = {
     "fk": ("fk.cu", "stages.cuh", "exmy.cuh", "common.cuh"),
-    "collision": ("collision.cu", "stages.cuh", "exmy.cuh", "common.cuh"),
+    "collision": ("collision.cu", "stages.cuh", "grid.cuh", "exmy.cuh", "common.cuh"),
     "backward": ("backward.cu", "stages.cuh", "exmy.cuh", "common.cuh"),
 }
 
@@ -262,6 +262,29 @@ def collision_flops_per_config(w) -> int:
     1 mul, 2 fma, 1 mul = 9 FLOP).  Exact distances of the pairs that pass
     come on top; they are data-dependent and not counted."""
     return 10 * w.robot.n_spheres * w.scene.n_cuboids + 9 * w.robot.n_pairs
+
+
+def broad_phase_leg(w, ev32, q, n, args, flush, torch):
+    """What the two broad phases buy: the same step with the plain loop over
+    every cuboid (no grid), and the grid's build time.  (The self-pair
+    clusters are part of the kernel and always on.)"""
+    from paper_2310_07854_gb300.path import Evaluator
+    import numpy as np
+    ev = Evaluator(ev32.robot, w.scene, w.params, n, F.FP32_TABLE, grid_cells=None)
+    per = time_steps(ev, q, n, args.steps, args.warmup, flush, torch)
+    reach = float(np.max(w.robot.sphere_local[:, 3]))
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(5):
+        g0.record()
+        ev.scene.build_grid(reach, w.params.eta, ev32.scene.grid_cells)
+        g1.record()
+        torch.cuda.synchronize()
+        ts.append(g0.elapsed_time(g1))
+    return {"grid_cells_per_axis": ev32.scene.grid_cells, "grid_bytes": int(ev32.scene.grid.numel()),
+            "grid_build_ms": statistics.median(ts),
+            "without_grid": {"configs_per_s": n * args.steps / (sum(per["step"]) / 1000.0),
+                             "collision_ms": statistics.mean(per["collision"])}}
 
 
 def fp32_peak_tflops(peaks) -> float:
@@ -665,6 +688,9 @@ def main():
         peak_alu = fp32_peak_tflops(peaks)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
                 "frac": ach / peak_alu, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
+                "work": "the method's bounding tests of all S*O sphere/cuboid pairs and all self pairs; "
+                        "the kernel's broad phases (grid cells, sphere clusters) skip most of them, so this "
+                        "is the rate of the method's work, not of instructions executed",
                 "traffic": None if traffic is None else traffic * n,
                 "algorithmic_flops_per_launch": fpc * n, "algorithmic_bytes_per_launch": bpc[dom] * n}
     else:
@@ -715,6 +741,7 @@ def main():
                 dram[name][k] = {"ms": ms, "hbm_frac": bp[k] * nb / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]}
         del ebig, ebv, qb
 
+    broad = broad_phase_leg(w, ev32, q, n, args, flush, torch)
     fused = fused_leg(w, q, n, vtable, args, flush, torch)
     ev32.fk(q, n)
     swept = swept_leg(w, ev32, n, args, flush, torch)
@@ -745,6 +772,7 @@ def main():
                      "speedup_vs_fp32": value_v / value, "ms_per_step": tv / args.steps,
                      "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale},
             "stages": stages,
+            "broad_phase": broad,
             "fused_single_launch": fused,
             "swept": swept,
             "ik": ik_res,

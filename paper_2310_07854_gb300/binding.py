@@ -277,6 +277,7 @@ class DeviceScene:
         self.half_ext = torch.as_tensor(half, device=device)
         self.c = vapr_scene(n, 0, self.pose.data_ptr(), self.half_ext.data_ptr(), None)
         self.grid = None
+        self.grid_cells = None
 
     def build_grid(self, reach: float, eta: float, cells: int = 64, stream=None):
         """Builds the broad-phase grid for spheres of radius <= reach and this
@@ -288,11 +289,13 @@ class DeviceScene:
         buf = torch.empty(nb, dtype=torch.uint8, device=self.pose.device)
         vapr_scene_grid_build(self, reach, eta, cells, buf, nb, stream)
         self.grid = buf
+        self.grid_cells = cells
         self.c.grid = buf.data_ptr()
         return self
 
     def drop_grid(self):
         self.grid = None
+        self.grid_cells = None
         self.c.grid = None
 
 

@@ -14,11 +14,20 @@ from . import formats as F
 
 class Evaluator:
     def __init__(self, robot, scene, params, n_max: int, table: F.FormatTable = F.FP32_TABLE,
-                 recompute_fk: bool = True, device: str = "cuda"):
+                 recompute_fk: bool = True, device: str = "cuda", grid_cells: int | None = 64):
+        """A scene given as host arrays gets a broad-phase grid of grid_cells
+        cells per axis (None: no grid); a DeviceScene is used as it is."""
+        import numpy as np
         import torch
         self.torch = torch
         self.robot = robot if isinstance(robot, B.DeviceRobot) else B.DeviceRobot(robot, device)
-        self.scene = scene if isinstance(scene, B.DeviceScene) else B.DeviceScene(scene, device)
+        if isinstance(scene, B.DeviceScene):
+            self.scene = scene
+        else:
+            self.scene = B.DeviceScene(scene, device)
+            if grid_cells:
+                reach = float(np.max(self.robot.host.sphere_local[:, 3]))
+                self.scene.build_grid(reach, params.eta, grid_cells)
         self.params = B.cost_params(params)
         self.table = table
         self.ctable = B.to_c_table(table)  # built once: calls pass the C struct
