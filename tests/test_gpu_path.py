@@ -166,7 +166,7 @@ def _big_robot():
 
 
 @pytest.mark.parametrize("case", ["n1", "n129", "n1000_no_pairs", "one_sphere", "no_cuboids",
-                                  "max_sizes", "shuffled_spheres"])
+                                  "max_sizes", "shuffled_spheres", "reversed_pairs", "duplicate_pairs"])
 def test_edge_cases(case):
     robot, n, O = synth.make_robot(2), 64, 8
     if case == "n1":
@@ -188,6 +188,14 @@ def test_edge_cases(case):
         inv = np.argsort(perm)
         robot = synth.Robot(robot.joint_fixed, robot.sphere_local[perm], robot.sphere_link[perm],
                             np.sort(inv[robot.pairs], axis=1).astype(np.int32))
+    elif case == "reversed_pairs":  # every pair listed as (j, i), in reverse order
+        robot = synth.Robot(robot.joint_fixed, robot.sphere_local, robot.sphere_link,
+                            np.ascontiguousarray(robot.pairs[::-1, ::-1]))
+    elif case == "duplicate_pairs":  # some pairs named twice, one of them reversed: each counts
+        pr = np.asarray(robot.pairs)
+        extra = np.concatenate([pr[:40], pr[100:101, ::-1]])
+        robot = synth.Robot(robot.joint_fixed, robot.sphere_local, robot.sphere_link,
+                            np.ascontiguousarray(np.concatenate([pr, extra]).astype(np.int32)))
     scene = synth.make_scene(4, O)
     q = synth.make_q(9, n, limit=np.pi) if robot.n_joints == 7 else \
         np.random.default_rng(9).uniform(-2.8, 2.8, (n, robot.n_joints)).astype(np.float32)
