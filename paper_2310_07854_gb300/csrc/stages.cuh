@@ -166,6 +166,33 @@ __device__ __forceinline__ void fk_store_pos(const RobotSm& r, int S, const floa
     });
 }
 
+// The same row through a per-warp float staging row (stage: `words` floats,
+// 16-byte aligned, words 3S.. zero): lanes take spheres, so the three
+// centre values of a sphere share one read of its transform rows; then
+// lanes take the words, FP32 rows as 16-byte copies.  The values are those
+// of fk_store_pos, bit for bit.
+template <int K>
+__device__ __forceinline__ void fk_store_pos_staged(const RobotSm& r, int S, const float4* T, uint32_t* out,
+                                                    int words, const DevFmt& f, int lane, float* stage) {
+  for (int s = lane; s < S; s += 32) {
+    const int l = r.link0[s];
+    const float4 p = r.sph[s];
+    const float4 r0 = T[3 * l], r1 = T[3 * l + 1], r2 = T[3 * l + 2];
+    stage[3 * s] = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
+    stage[3 * s + 1] = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
+    stage[3 * s + 2] = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
+  }
+  __syncwarp();
+  if constexpr (K == KIND_F32) {
+    for (int c = lane; c < words / 4; c += 32)
+      reinterpret_cast<uint4*>(out)[c] = reinterpret_cast<const uint4*>(stage)[c];
+  } else {
+    const int nv = 3 * S;
+    for (int w = lane; w < words; w += 32) out[w] = pack_word_t<K>(w, nv, f, [&](int i) { return stage[i]; });
+  }
+  __syncwarp();
+}
+
 // Packed link-transform row (element e of T_j is value 12 j + e).
 template <int K>
 __device__ __forceinline__ void fk_store_xform(int J, const float4* T, uint32_t* out, int words,
