@@ -126,14 +126,14 @@ typedef struct {
  * r + eta + half diagonal), each cell holding the bitmask of the cuboids
  * whose test a sphere centred in it can pass.  With scene->grid set, the
  * collision stage (vapr_collision_cost, vapr_cost_grad, vapr_ik_*,
- * vapr_surrogate_collision_cost) visits only the cuboids of a sphere's cell,
- * in cuboid order, with the same bounding test and exact distance: its
- * outputs are bit-identical to the plain loop over every cuboid.  Each
- * launch checks on the device that the grid was built for the scene's
- * current pose and half-extent words (a hash), the same eta and sphere
- * radii all in [0, reach], and otherwise runs the plain loop, so a stale
- * grid costs speed, never correctness.  Not used by the multi-problem
- * launch or the swept cost. */
+ * vapr_surrogate_collision_cost, vapr_swept_cost) visits only the cuboids
+ * of a sphere's (or swept point's) cell, in cuboid order, with the same
+ * bounding test and exact distance: its outputs are bit-identical to the
+ * plain loop over every cuboid.  Each launch checks on the device that the
+ * grid was built for the scene's current pose and half-extent words (a
+ * hash), the same eta and sphere radii all in [0, reach], and otherwise
+ * runs the plain loop, so a stale grid costs speed, never correctness.
+ * The multi-problem launch does not use it. */
 #define VAPR_GRID_MAX_CELLS 128
 /* bytes of a grid for n_cuboids cuboids and at most cells_per_axis cells
  * along each axis (1..VAPR_GRID_MAX_CELLS); 0 when out of range */

@@ -92,8 +92,19 @@ __global__ void __launch_bounds__(SW_WARPS * 32) swept_kernel(SweptArgs a) {
     Pp[s] = w.P[s];
   }
   __syncthreads();
+  const GridHeader* grid = grid_check(a.sc, a.r, a.eta);  // null: every cuboid
+  const uint2* cells = grid ? grid_cells(a.sc) : nullptr;
+  // the terms of two points, through the scene grid when there is one
+  auto terms = [&](const float4& xa, bool va, const float4& xb, bool vb, float4& ta, float4& tb) {
+    if (grid) {
+      env_grid(sm, *grid, cells, va, xa, a.eta, a.w_c, ta);
+      env_grid(sm, *grid, cells, vb, xb, a.eta, a.w_c, tb);
+    } else {
+      point_terms(sm, a.sc.O, xa, va, xb, vb, a.eta, a.w_c, ta, tb);
+    }
+  };
 
-  const int S = a.r.S, O = a.sc.O, K = a.samples, H = a.horizon;
+  const int S = a.r.S, K = a.samples, H = a.horizon;
   const float invK = 1.f / (float)K;
   const int64_t chunks_per_traj = (H + SW_CHUNK - 1) / SW_CHUNK;
   const int64_t n_chunks = (a.n / H) * chunks_per_traj;
@@ -126,7 +137,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32) swept_kernel(SweptArgs a) {
         for (int k = 1; k < K; ++k) {
           const float al = (float)k * invK;
           float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
-          point_terms(sm, O, lerp4(pa, ca, al), va, lerp4(pb, cb, al), vb, a.eta, a.w_c, ta, tb);
+          terms(lerp4(pa, ca, al), va, lerp4(pb, cb, al), vb, ta, tb);
           c0 = make_float3(fmaf(al, ta.y, c0.x), fmaf(al, ta.z, c0.y), fmaf(al, ta.w, c0.z));
           c1 = make_float3(fmaf(al, tb.y, c1.x), fmaf(al, tb.z, c1.y), fmaf(al, tb.w, c1.z));
         }
@@ -151,7 +162,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32) swept_kernel(SweptArgs a) {
         for (int k = 0; k < K; ++k) {
           const float al = (float)k * invK;
           float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta;
-          point_terms(sm, O, lerp4(ca, na, al), va, lerp4(cb, nb, al), vb, a.eta, a.w_c, ta, tb);
+          terms(lerp4(ca, na, al), va, lerp4(cb, nb, al), vb, ta, tb);
           const float wo = last ? 1.f : 1.f - al;
           Da += ta.x;
           Db += tb.x;
@@ -220,7 +231,6 @@ extern "C" vapr_status vapr_swept_cost(const vapr_robot* robot, const vapr_scene
   if (!params) return VAPR_ERR_INVALID_ARG;
   SceneArgs sc;
   if ((v = check_scene(scene, &sc)) != VAPR_OK) return v;
-  sc.grid = nullptr;  // the swept loop visits every cuboid
   if (n < 0 || horizon < 1 || samples < 1) return VAPR_ERR_INVALID_ARG;
   if (samples > VAPR_MAX_SWEPT_SAMPLES) return VAPR_ERR_TOO_LARGE;
   if (n % horizon) return VAPR_ERR_INVALID_ARG;

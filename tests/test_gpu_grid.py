@@ -228,3 +228,27 @@ def test_grid_in_cost_grad_ik_and_surrogate():
         out += [cost.cpu().numpy().view(np.uint32), dist.cpu().numpy(), grad.cpu().numpy()]
         res.append(out)
     assert_same(res[0], res[1])
+
+
+@pytest.mark.parametrize("name,K", [("sweep_1024", 4), ("particle_32768", 3), ("single_128", 1)])
+def test_grid_in_swept_cost(name, K):
+    """The swept points go through the same grid: same bits with and without."""
+    import torch
+    w = synth.make_workload(name)
+    rd = B.DeviceRobot(w.robot)
+    S = w.robot.n_spheres
+    pos = B.alloc_packed(w.n, 3 * S, F.FP32)
+    B.vapr_fk(rd, to_dev(w.q), w.n, F.FP32_TABLE, pos)
+    res = []
+    for grid in (False, True):
+        sd = B.DeviceScene(w.scene)
+        if grid:
+            sd.build_grid(reach_of(w.robot), w.params.eta, 48)
+        for table in TABLES[:2]:
+            cost = torch.empty(w.n, device="cuda")
+            dist = B.alloc_packed(w.n, S, table.dist)
+            grad = B.alloc_packed(w.n, 3 * S, table.grad)
+            B.vapr_swept_cost(rd, sd, w.params, pos, w.n, w.horizon, K, table, cost, dist, grad)
+            res.append([cost.cpu().numpy().view(np.uint32), dist.cpu().numpy(), grad.cpu().numpy()])
+    assert_same(res[0], res[2])
+    assert_same(res[1], res[3])
