@@ -149,19 +149,27 @@ __global__ void ik_terms(IkArgs a, IkWork w, DevFmt fj, int64_t jstride, int N) 
 }
 
 // Steepest descent scaled so that the largest joint move is step0.
-__device__ __forceinline__ void restart_dir(const float* g, float* d, int J, float step0) {
+template <int JT>
+__device__ __forceinline__ void restart_dir(const float* g, float* d, float step0) {
   float mx = 0.f;
-  for (int j = 0; j < J; ++j) mx = fmaxf(mx, fabsf(g[j]));
+#pragma unroll
+  for (int j = 0; j < JT; ++j) mx = fmaxf(mx, fabsf(g[j]));
   const float s = mx > 0.f ? step0 / mx : 0.f;
-  for (int j = 0; j < J; ++j) d[j] = -g[j] * s;
+#pragma unroll
+  for (int j = 0; j < JT; ++j) d[j] = -g[j] * s;
 }
 
-// init: candidates are the seeds themselves (N = 1) and nothing is compared.
-__global__ void ik_update(IkArgs a, float* __restrict__ q, IkWork w, float* __restrict__ cost,
-                          int32_t* __restrict__ pick, int N, int init) {
+// One thread per seed; JT = the arm's joint count at compile time, so the
+// per-joint vectors live in registers.  init: candidates are the seeds
+// themselves (N = 1) and nothing is compared.
+template <int JT>
+__global__ void __launch_bounds__(64) ik_update(IkArgs a, float* __restrict__ q, IkWork w,
+                                                float* __restrict__ cost, int32_t* __restrict__ pick,
+                                                int N, int init) {
+  constexpr int J = JT;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  const int J = a.J, m = a.m;
+  const int m = a.m;
   int best = 0;
   float fb = w.ctot[i * N];
   for (int k = 1; k < N; ++k) {
@@ -172,7 +180,8 @@ __global__ void ik_update(IkArgs a, float* __restrict__ q, IkWork w, float* __re
     }
   }
   const int64_t cb = i * N + best;
-  float gn[VAPR_MAX_JOINTS], qn[VAPR_MAX_JOINTS];
+  float gn[J], qn[J];
+#pragma unroll
   for (int j = 0; j < J; ++j) {
     gn[j] = w.cgrad[cb * J + j];
     qn[j] = w.cq[cb * J + j];
@@ -183,63 +192,102 @@ __global__ void ik_update(IkArgs a, float* __restrict__ q, IkWork w, float* __re
   float* d = w.d + i * J;
   if (init || a.scales[best] == 0.f) {
     cnt = 0;
-    restart_dir(gn, d, J, a.step0);
+    float dn[J];
+    restart_dir<J>(gn, dn, a.step0);
+#pragma unroll
+    for (int j = 0; j < J; ++j) d[j] = dn[j];
   } else {
     float sy = 0.f;
+#pragma unroll
     for (int j = 0; j < J; ++j) sy = fmaf(qn[j] - q[i * J + j], gn[j] - w.g[i * J + j], sy);
     if (sy > 0.f) {
       if (cnt == m) {  // drop the oldest pair
         for (int k = 0; k + 1 < m; ++k)
+#pragma unroll
           for (int j = 0; j < J; ++j) {
             S[k * J + j] = S[(k + 1) * J + j];
             Y[k * J + j] = Y[(k + 1) * J + j];
           }
         --cnt;
       }
+#pragma unroll
       for (int j = 0; j < J; ++j) {
         S[cnt * J + j] = qn[j] - q[i * J + j];
         Y[cnt * J + j] = gn[j] - w.g[i * J + j];
       }
       ++cnt;
     }
+    float dd[J];
     if (cnt == 0) {
-      restart_dir(gn, d, J, a.step0);
+      restart_dir<J>(gn, dd, a.step0);
     } else {  // two-loop recursion, H0 = (s.y / y.y) I of the newest pair
-      float dd[VAPR_MAX_JOINTS], alpha[VAPR_IK_MAX_HISTORY], rho[VAPR_IK_MAX_HISTORY];
+      float alpha[VAPR_IK_MAX_HISTORY], rho[VAPR_IK_MAX_HISTORY];
+#pragma unroll
       for (int j = 0; j < J; ++j) dd[j] = -gn[j];
-      for (int k = cnt - 1; k >= 0; --k) {
+#pragma unroll
+      for (int k = VAPR_IK_MAX_HISTORY - 1; k >= 0; --k) {
+        if (k >= cnt) continue;
         float s_y = 0.f, s_q = 0.f;
+#pragma unroll
         for (int j = 0; j < J; ++j) {
           s_y = fmaf(S[k * J + j], Y[k * J + j], s_y);
           s_q = fmaf(S[k * J + j], dd[j], s_q);
         }
         rho[k] = 1.f / s_y;
         alpha[k] = rho[k] * s_q;
+#pragma unroll
         for (int j = 0; j < J; ++j) dd[j] = fmaf(-alpha[k], Y[k * J + j], dd[j]);
       }
       float s_y = 0.f, y_y = 0.f;
+#pragma unroll
       for (int j = 0; j < J; ++j) {
         s_y = fmaf(S[(cnt - 1) * J + j], Y[(cnt - 1) * J + j], s_y);
         y_y = fmaf(Y[(cnt - 1) * J + j], Y[(cnt - 1) * J + j], y_y);
       }
       const float gam = s_y / y_y;
+#pragma unroll
       for (int j = 0; j < J; ++j) dd[j] *= gam;
-      for (int k = 0; k < cnt; ++k) {
+#pragma unroll
+      for (int k = 0; k < VAPR_IK_MAX_HISTORY; ++k) {
+        if (k >= cnt) continue;
         float yr = 0.f;
+#pragma unroll
         for (int j = 0; j < J; ++j) yr = fmaf(Y[k * J + j], dd[j], yr);
         const float beta = rho[k] * yr;
+#pragma unroll
         for (int j = 0; j < J; ++j) dd[j] = fmaf(alpha[k] - beta, S[k * J + j], dd[j]);
       }
-      for (int j = 0; j < J; ++j) d[j] = dd[j];
     }
+#pragma unroll
+    for (int j = 0; j < J; ++j) d[j] = dd[j];
   }
   w.mcount[i] = cnt;
+#pragma unroll
   for (int j = 0; j < J; ++j) {
     w.g[i * J + j] = gn[j];
     if (!init) q[i * J + j] = qn[j];
   }
   if (cost) cost[i] = fb;
   if (pick) pick[i] = best;
+}
+
+template <int JT>
+static void launch_update_j(const IkArgs& a, float* q, const IkWork& w, float* cost, int32_t* pick, int N,
+                            int init, cudaStream_t st) {
+  ik_update<JT><<<(int)((a.n + 63) / 64), 64, 0, st>>>(a, q, w, cost, pick, N, init);
+}
+
+static void launch_update(const IkArgs& a, float* q, const IkWork& w, float* cost, int32_t* pick, int N,
+                          int init, cudaStream_t st) {
+  switch (a.J) {
+#define VAPR_IK_J(n) \
+  case n: launch_update_j<n>(a, q, w, cost, pick, N, init, st); break;
+    VAPR_IK_J(1) VAPR_IK_J(2) VAPR_IK_J(3) VAPR_IK_J(4) VAPR_IK_J(5) VAPR_IK_J(6) VAPR_IK_J(7)
+    VAPR_IK_J(8) VAPR_IK_J(9) VAPR_IK_J(10) VAPR_IK_J(11) VAPR_IK_J(12) VAPR_IK_J(13)
+    VAPR_IK_J(14) VAPR_IK_J(15) VAPR_IK_J(16)
+#undef VAPR_IK_J
+    default: break;
+  }
 }
 
 static vapr_status check_ik(const vapr_robot* robot, const vapr_scene* scene, const vapr_cost_params* params,
@@ -303,7 +351,7 @@ static cudaError_t run_iteration(const RobotArgs& r, const vapr_scene* scene, co
   if ((e = launch_backward(r, w.cq, none, G, nullptr, c, Jg, st)) != cudaSuccess) return e;
   ik_terms<<<(int)((c + 127) / 128), 128, 0, st>>>(a, w, Jg.f, Jg.stride, N);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ik_update<<<(int)((a.n + 127) / 128), 128, 0, st>>>(a, q, w, cost, pick, N, init ? 1 : 0);
+  launch_update(a, q, w, cost, pick, N, init ? 1 : 0, st);
   return cudaGetLastError();
 }
 
