@@ -719,10 +719,22 @@ def main():
     for _ in range(args.steps):
         ev32.step_host(qh, ch, jh, qd)
     barrier()
+    te_eager = max_over_ranks(time.perf_counter() - t0)
+    run = ev32.host_step_graph(qh, ch, jh, qd)  # the same step as one graph launch
+    for _ in range(args.warmup):
+        run()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    barrier()
     te = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": world * n * args.steps / te, "unit": "configs/s",
            "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(ch.numel() * 4 + jh.numel() * 4),
-           "launches_per_step": 4}
+           "call": "Evaluator.host_step_graph: H2D q, FK, collision, backward, unpack J, D2H C and J, "
+                   "one graph launch and a host wait per step",
+           "eager_step_host": {"value": world * n * args.steps / te_eager, "unit": "configs/s",
+                               "launches_per_step": 4, "copies_per_step": 3}}
 
     dram = None
     if not args.no_dram_scale:

@@ -122,6 +122,33 @@ class Evaluator:
         st.synchronize()
         return cost_host, jgrad_host
 
+    def host_step_graph(self, q_host, cost_host, jgrad_host, q_dev):
+        """The end-to-end step of ``step_host`` captured once in a CUDA graph:
+        the host-to-device copy of q, the path, the joint-gradient unpack and
+        the device-to-host copies of C and J replay as one launch.  Returns a
+        function that runs one step on the current contents of q_host and
+        returns after cost_host and jgrad_host hold the results.  The buffers
+        are bound at capture time."""
+        torch = self.torch
+        n = q_host.shape[0]
+        st = torch.cuda.Stream()
+        self.step_host(q_host, cost_host, jgrad_host, q_dev, st)  # fills the launch caches
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            q_dev[:n].copy_(q_host, non_blocking=True)
+            self.cost_grad(q_dev, n, None, st)
+            self.unpack_jgrad(n, st)
+            cost_host.copy_(self.cost[:n], non_blocking=True)
+            jgrad_host.copy_(self.jgrad_f32[:n], non_blocking=True)
+
+        def run():
+            with torch.cuda.stream(st):
+                g.replay()
+            st.synchronize()
+            return cost_host, jgrad_host
+        run.graph = g
+        return run
+
     def bytes_per_config(self) -> dict:
         """Algorithmic bytes per configuration of each stage (packed rows,
         unpadded; robot and scene tables excluded)."""

@@ -50,3 +50,34 @@ def test_cost_grad_fp32_parity():
     check_fp32(cost.cpu().numpy(), col["cost"], what="C")
     ok = ~col["kink"].any(1)
     check_fp32(decode_packed(jg, 7, F.FP32), want, mask=np.repeat(ok[:, None], 7, 1), what="J")
+
+
+def test_host_step_and_its_graph():
+    """step_host (pinned host q in, C and J out) and its captured graph give
+    the device path's results, and each replay reads the current q_host."""
+    import torch
+    from paper_2310_07854_gb300.path import Evaluator
+    w = synth.make_workload("sweep_1024")
+    n, J = w.n, w.robot.n_joints
+    ev = Evaluator(w.robot, w.scene, w.params, n)
+    qh = torch.empty((n, J), dtype=torch.float32).pin_memory()
+    ch = torch.empty(n, dtype=torch.float32).pin_memory()
+    jh = torch.empty((n, J), dtype=torch.float32).pin_memory()
+    qd = torch.empty((n, J), dtype=torch.float32, device="cuda")
+
+    def device_path(qnp):
+        q = to_dev(qnp)
+        ev.cost_grad(q, n)
+        return ev.cost[:n].cpu().clone(), ev.unpack_jgrad(n).cpu().clone()
+
+    qh.copy_(torch.as_tensor(w.q))
+    c1, j1 = ev.step_host(qh, ch, jh, qd)
+    want_c, want_j = device_path(w.q)
+    assert torch.equal(c1, want_c) and torch.equal(j1, want_j)
+    run = ev.host_step_graph(qh, ch, jh, qd)
+    for seed in (31, 32):
+        qn = synth.make_q(seed, n)
+        qh.copy_(torch.as_tensor(qn))
+        c2, j2 = run()
+        want_c, want_j = device_path(qn)
+        assert torch.equal(c2, want_c) and torch.equal(j2, want_j), seed
