@@ -295,6 +295,15 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
                                  const SelfScratch& t, float eta_s) {
   const int NP = r.NP, NC = rb.n_cl[0], keys = NC * NC, kw = (keys + 31) / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (NP == 0) {  // no pairs: an empty table (the scratch is sized for none)
+    if (threadIdx.x == 0) {
+      m.self_meta[0] = 0;
+      m.self_meta[1] = (int)__float_as_uint(eta_s);
+      m.cp_start[0] = 0;
+    }
+    __syncthreads();
+    return;
+  }
   for (int k = threadIdx.x; k < kw; k += blockDim.x) t.keymap[k] = 0u;
   __syncthreads();
   for (int p = threadIdx.x; p < NP; p += blockDim.x) {
