@@ -97,8 +97,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32) swept_kernel(SweptArgs a) {
   // the terms of two points, through the scene grid when there is one
   auto terms = [&](const float4& xa, bool va, const float4& xb, bool vb, float4& ta, float4& tb) {
     if (grid) {
-      env_grid(sm, *grid, cells, va, xa, a.eta, a.w_c, ta);
-      env_grid(sm, *grid, cells, vb, xb, a.eta, a.w_c, tb);
+      env_grid2(sm, *grid, cells, va, xa, vb, xb, a.eta, a.w_c, ta, tb);
     } else {
       point_terms(sm, a.sc.O, xa, va, xb, vb, a.eta, a.w_c, ta, tb);
     }
