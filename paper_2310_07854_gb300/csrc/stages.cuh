@@ -400,7 +400,8 @@ __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp&
 // Applies the listed active self pairs to acc, sphere-major: each lane takes
 // its spheres (up to two per 64) and walks the list in order, subtracting u
 // where it is the pair's first sphere and adding it where it is the second,
-// so every sphere receives its self terms in pair order.
+// so every sphere receives its self terms in list order (the order in which
+// self_pairs tested them: the cluster-pair table's order).
 __device__ __forceinline__ void apply_self_pairs(const CollWarp& w, int S, int n_act, int lane) {
   for (int base = 0; base < S; base += 64) {
     const int sa = base + lane, sb = sa + 32;
