@@ -231,10 +231,15 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_sha(stage: str) -> str:
-    """Hash of every source file the stage's kernel is compiled from."""
+    """Hash of every source file the stage's kernel is compiled from, with
+    comments and blank lines left out (a comment edit is not a kernel change)."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[stage]:
-        h.update(open(os.path.join(ROOT, "paper_2310_07854_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2310_07854_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(l.rstrip() for l in text.splitlines() if l.strip()).encode())
     return h.hexdigest()[:16]
 
 
