@@ -51,11 +51,13 @@ def test_grid_outputs_bit_identical(name, table, cells):
     assert_same(outputs(gp, pos, w.n, table), plain)
 
 
-@pytest.mark.parametrize("n_cuboids,extent", [(0, 0.75), (1, 0.3), (65, 0.9), (200, 1.2), (130, 0.2)])
+@pytest.mark.parametrize("n_cuboids,extent", [(0, 0.75), (1, 0.3), (65, 0.9), (200, 1.2), (130, 0.2),
+                                               (1024, 1.5)])
 @pytest.mark.parametrize("cells", [5, 32, 100])
 def test_grid_random_scenes(n_cuboids, extent, cells):
-    """Several 64-cuboid chunks, an empty scene, a scene far smaller than the
-    arm's reach (most spheres outside the grid), a dense one."""
+    """Several 64-cuboid chunks (up to the 1024-cuboid maximum), an empty
+    scene, a scene far smaller than the arm's reach (most spheres outside
+    the grid), a dense one."""
     w = synth.make_workload("sweep_1024")
     w.scene = synth.make_scene(11 + n_cuboids, n_cuboids, extent=extent)
     gp = GpuPath(w.robot, w.scene, w.params)
