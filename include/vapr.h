@@ -133,7 +133,7 @@ typedef struct {
  * grid was built for the scene's current pose and half-extent words (a
  * hash), the same eta and sphere radii all in [0, reach], and otherwise
  * runs the plain loop, so a stale grid costs speed, never correctness.
- * The multi-problem launch does not use it. */
+ * The multi-problem launch uses each problem's scene grid the same way. */
 #define VAPR_GRID_MAX_CELLS 128
 /* bytes of a grid for n_cuboids cuboids and at most cells_per_axis cells
  * along each axis (1..VAPR_GRID_MAX_CELLS); 0 when out of range */

@@ -15,7 +15,11 @@ from . import formats as F
 
 class BatchedEvaluator:
     def __init__(self, problems, table: F.FormatTable = F.FP32_TABLE, tile: int = 128,
-                 wait_limit_us: int = 0, deferred=(), keep_dist: bool = False, device="cuda"):
+                 wait_limit_us: int = 0, deferred=(), keep_dist: bool = False, device="cuda",
+                 grid_cells: int | None = 32):
+        """Each problem's scene gets a broad-phase grid of grid_cells cells per
+        axis (None: none); it changes no result."""
+        import numpy as np
         import torch
         self.torch = torch
         self.table = table
@@ -25,6 +29,8 @@ class BatchedEvaluator:
         arr = (B.vapr_problem * len(problems))()
         for i, w in enumerate(problems):
             rd, sd = B.DeviceRobot(w.robot, device), B.DeviceScene(w.scene, device)
+            if grid_cells and w.scene.n_cuboids > 0:
+                sd.build_grid(float(np.max(w.robot.sphere_local[:, 3])), w.params.eta, grid_cells)
             q = torch.as_tensor(w.q, device=device)
             cost = torch.full((w.n,), float("nan"), dtype=torch.float32, device=device)
             dist = B.alloc_packed(w.n, w.robot.n_spheres, table.dist, device) if keep_dist else None

@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(BT_BLOCK) batched_kernel(BatchArgs a) {
   carve_batch(b, a, rb, sm, w, warp, sU, sQ, sItem, self_scr);
   uint8_t* scratch = a.scratch + (int64_t)blockIdx.x * a.scratch_block;
   int cur = -1;
+  const GridHeader* grid = nullptr;  // the current problem's scene grid, when usable
+  const uint2* cells = nullptr;
   for (;;) {
     if (threadIdx.x == 0) {
       const int item = atomicAdd(a.counter, 1);
@@ -154,6 +156,8 @@ __global__ void __launch_bounds__(BT_BLOCK) batched_kernel(BatchArgs a) {
       load_clusters(J, S, rb);
       load_self(P.r, rb, sm, self_scr, P.eta_s);
       init_coll_warp(P.r, w, lane);
+      grid = grid_check(P.sc, P.r, P.eta);  // block-wide; null: every cuboid
+      cells = grid ? grid_cells(P.sc) : nullptr;
       cur = it.problem;
     }
     const int tstride = (3 * J) | 1, kstride = (2 * J) | 1;
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(BT_BLOCK) batched_kernel(BatchArgs a) {
       out.grad = reinterpret_cast<uint32_t*>(grow0 + r * P.grad_stride);
       collision_config<true>(P.r, P.sc.O, rb, sm, w,
                              reinterpret_cast<const uint32_t*>(prow0 + r * P.pos_stride), a.fP, a.fD,
-                             a.fG, P.eta, P.w_c, P.w_s, out, lane);
+                             a.fG, P.eta, P.w_c, P.w_s, out, lane, nullptr, 0.f, grid, cells);
     }
     __syncthreads();
     // ---- backward: one thread per configuration, G from scratch
@@ -258,12 +262,12 @@ static vapr_status layout(const vapr_problem* pr, int32_t np, const vapr_format_
     if (p.n > 0 && (!p.q || !p.cost || !p.jgrad_packed)) return VAPR_ERR_INVALID_ARG;
     if ((p.scene.n_cuboids > 0 && (!al(p.scene.pose, 16) || !al(p.scene.half_ext, 4))) ||
         !al(p.q, 4) || !al(p.cost, 4) || !al(p.dcost, 4) || !al(p.dist_packed, 16) ||
-        !al(p.jgrad_packed, 16))
+        !al(p.jgrad_packed, 16) || !al(p.scene.grid, 16))
       return VAPR_ERR_MISALIGNED;
     d.sc.O = p.scene.n_cuboids;
     d.sc.pose = p.scene.pose;
     d.sc.half = p.scene.half_ext;
-    d.sc.grid = nullptr;  // every tile visits every cuboid of its problem
+    d.sc.grid = p.scene.grid;  // checked against the problem on the device, as everywhere
     d.eta = p.params.eta;
     d.eta_s = p.params.eta_self;
     d.w_c = p.params.w_coll;

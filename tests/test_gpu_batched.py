@@ -32,13 +32,16 @@ def _reference(w, table):
     return cost, jg
 
 
-@pytest.mark.parametrize("spec,tile", [("", 128), ("", 32), ("", 256),
-                                       ("P=E5M10,D=E2M1,G=E2M1,J=E4M3", 64)])
-def test_batched_equals_per_problem(problems, spec, tile):
+@pytest.mark.parametrize("spec,tile,grid", [("", 128, 32), ("", 32, 32), ("", 256, 32),
+                                            ("P=E5M10,D=E2M1,G=E2M1,J=E4M3", 64, 32), ("", 128, None),
+                                            ("", 64, 96)])
+def test_batched_equals_per_problem(problems, spec, tile, grid):
+    """Each problem's scene grid (or none) leaves the results as the plain
+    per-problem path gives them."""
     import torch
     from paper_2310_07854_gb300.batched import BatchedEvaluator
     table = F.FormatTable.parse(spec) if spec else F.FP32_TABLE
-    ev = BatchedEvaluator(problems, table, tile=tile)
+    ev = BatchedEvaluator(problems, table, tile=tile, grid_cells=grid)
     ev.eval()
     torch.cuda.synchronize()
     assert ev.device_status() == 0
