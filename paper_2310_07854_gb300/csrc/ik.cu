@@ -17,9 +17,10 @@ namespace vapr {
 struct IkWork {
   float* g;      // [n][J] gradient at q
   float* d;      // [n][J] direction
-  float* S;      // [n][m][J] oldest first
+  float* S;      // [n][m][J] a ring: pair k (0 = oldest) in slot (mhead + k) mod m
   float* Y;      // [n][m][J]
   int* mcount;   // [n]
+  int* mhead;    // [n]
   float* cq;     // [n N][J] candidates
   float* ccoll;  // [n N] collision cost of the candidates
   uint8_t* cjg;  // [n N] packed joint-gradient rows (table->jgrad)
@@ -46,6 +47,7 @@ static IkWork carve_ik(void* base, const RobotArgs& r, int64_t n, int N, int m, 
   w.S = reinterpret_cast<float*>(take((size_t)n * m * r.J * 4));
   w.Y = reinterpret_cast<float*>(take((size_t)n * m * r.J * 4));
   w.mcount = reinterpret_cast<int*>(take((size_t)n * 4));
+  w.mhead = reinterpret_cast<int*>(take((size_t)n * 4));
   w.cq = reinterpret_cast<float*>(take((size_t)c * r.J * 4));
   w.ccoll = reinterpret_cast<float*>(take((size_t)c * 4));
   w.cjg = take((size_t)c * row_bytes(r.J, t->jgrad));
@@ -189,9 +191,15 @@ __global__ void __launch_bounds__(64) ik_update(IkArgs a, float* __restrict__ q,
   float* S = w.S + i * m * J;
   float* Y = w.Y + i * m * J;
   int cnt = init ? 0 : w.mcount[i];
+  int head = init ? 0 : w.mhead[i];
+  auto slot = [&](int k) {  // ring slot of pair k (0 = oldest)
+    const int sl = head + k;
+    return sl >= m ? sl - m : sl;
+  };
   float* d = w.d + i * J;
   if (init || a.scales[best] == 0.f) {
     cnt = 0;
+    head = 0;
     float dn[J];
     restart_dir<J>(gn, dn, a.step0);
 #pragma unroll
@@ -202,18 +210,14 @@ __global__ void __launch_bounds__(64) ik_update(IkArgs a, float* __restrict__ q,
     for (int j = 0; j < J; ++j) sy = fmaf(qn[j] - q[i * J + j], gn[j] - w.g[i * J + j], sy);
     if (sy > 0.f) {
       if (cnt == m) {  // drop the oldest pair
-        for (int k = 0; k + 1 < m; ++k)
-#pragma unroll
-          for (int j = 0; j < J; ++j) {
-            S[k * J + j] = S[(k + 1) * J + j];
-            Y[k * J + j] = Y[(k + 1) * J + j];
-          }
+        head = head + 1 == m ? 0 : head + 1;
         --cnt;
       }
+      const int sn = slot(cnt);
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        S[cnt * J + j] = qn[j] - q[i * J + j];
-        Y[cnt * J + j] = gn[j] - w.g[i * J + j];
+        S[sn * J + j] = qn[j] - q[i * J + j];
+        Y[sn * J + j] = gn[j] - w.g[i * J + j];
       }
       ++cnt;
     }
@@ -227,22 +231,26 @@ __global__ void __launch_bounds__(64) ik_update(IkArgs a, float* __restrict__ q,
 #pragma unroll
       for (int k = VAPR_IK_MAX_HISTORY - 1; k >= 0; --k) {
         if (k >= cnt) continue;
+        const float* Sk = S + slot(k) * J;
+        const float* Yk = Y + slot(k) * J;
         float s_y = 0.f, s_q = 0.f;
 #pragma unroll
         for (int j = 0; j < J; ++j) {
-          s_y = fmaf(S[k * J + j], Y[k * J + j], s_y);
-          s_q = fmaf(S[k * J + j], dd[j], s_q);
+          s_y = fmaf(Sk[j], Yk[j], s_y);
+          s_q = fmaf(Sk[j], dd[j], s_q);
         }
         rho[k] = 1.f / s_y;
         alpha[k] = rho[k] * s_q;
 #pragma unroll
-        for (int j = 0; j < J; ++j) dd[j] = fmaf(-alpha[k], Y[k * J + j], dd[j]);
+        for (int j = 0; j < J; ++j) dd[j] = fmaf(-alpha[k], Yk[j], dd[j]);
       }
       float s_y = 0.f, y_y = 0.f;
+      const float* Sn = S + slot(cnt - 1) * J;
+      const float* Yn = Y + slot(cnt - 1) * J;
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        s_y = fmaf(S[(cnt - 1) * J + j], Y[(cnt - 1) * J + j], s_y);
-        y_y = fmaf(Y[(cnt - 1) * J + j], Y[(cnt - 1) * J + j], y_y);
+        s_y = fmaf(Sn[j], Yn[j], s_y);
+        y_y = fmaf(Yn[j], Yn[j], y_y);
       }
       const float gam = s_y / y_y;
 #pragma unroll
@@ -250,18 +258,21 @@ __global__ void __launch_bounds__(64) ik_update(IkArgs a, float* __restrict__ q,
 #pragma unroll
       for (int k = 0; k < VAPR_IK_MAX_HISTORY; ++k) {
         if (k >= cnt) continue;
+        const float* Sk = S + slot(k) * J;
+        const float* Yk = Y + slot(k) * J;
         float yr = 0.f;
 #pragma unroll
-        for (int j = 0; j < J; ++j) yr = fmaf(Y[k * J + j], dd[j], yr);
+        for (int j = 0; j < J; ++j) yr = fmaf(Yk[j], dd[j], yr);
         const float beta = rho[k] * yr;
 #pragma unroll
-        for (int j = 0; j < J; ++j) dd[j] = fmaf(alpha[k] - beta, S[k * J + j], dd[j]);
+        for (int j = 0; j < J; ++j) dd[j] = fmaf(alpha[k] - beta, Sk[j], dd[j]);
       }
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) d[j] = dd[j];
   }
   w.mcount[i] = cnt;
+  w.mhead[i] = head;
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     w.g[i * J + j] = gn[j];
