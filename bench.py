@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--impl", default="vapr", choices=["vapr", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=list(synth.WORKLOADS))
     ap.add_argument("--table", default=VAPR_TABLE, help="format table of the VaPr leg")
+    ap.add_argument("--grid-cells", type=int, default=-1,
+                    help="cells per axis of the scene's broad-phase grid (0: none, -1: the evaluator's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dram-scale", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -275,6 +277,8 @@ def broad_phase_leg(w, ev32, q, n, args, flush, torch):
     clusters are part of the kernel and always on.)"""
     from paper_2310_07854_gb300.path import Evaluator
     import numpy as np
+    if ev32.scene.grid is None:
+        return {"grid_cells_per_axis": None}
     ev = Evaluator(ev32.robot, w.scene, w.params, n, F.FP32_TABLE, grid_cells=None)
     per = time_steps(ev, q, n, args.steps, args.warmup, flush, torch)
     reach = float(np.max(w.robot.sphere_local[:, 3]))
@@ -635,7 +639,8 @@ def main():
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
     flush = torch.zeros(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
     vtable = F.FormatTable.parse(args.table)
-    ev32 = Evaluator(w.robot, w.scene, w.params, n, F.FP32_TABLE)
+    ev32 = Evaluator(w.robot, w.scene, w.params, n, F.FP32_TABLE,
+                     grid_cells="auto" if args.grid_cells < 0 else (args.grid_cells or None))
     evv = Evaluator(ev32.robot, ev32.scene, w.params, n, vtable)
 
     def barrier():

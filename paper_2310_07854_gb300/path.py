@@ -12,11 +12,20 @@ from . import binding as B
 from . import formats as F
 
 
+def auto_grid_cells(n_cuboids: int, budget: int = 32 << 20) -> int:
+    """The finest grid (at most 128 cells per axis) whose bytes fit the budget."""
+    cells = 128
+    while cells > 8 and B.vapr_scene_grid_bytes(n_cuboids, cells) > budget:
+        cells -= 8
+    return cells
+
+
 class Evaluator:
     def __init__(self, robot, scene, params, n_max: int, table: F.FormatTable = F.FP32_TABLE,
-                 recompute_fk: bool = True, device: str = "cuda", grid_cells: int | None = 64):
+                 recompute_fk: bool = True, device: str = "cuda", grid_cells: int | str | None = "auto"):
         """A scene given as host arrays gets a broad-phase grid of grid_cells
-        cells per axis (None: no grid); a DeviceScene is used as it is."""
+        cells per axis ("auto": the finest up to 128 whose grid fits 32 MiB;
+        None: no grid); a DeviceScene is used as it is."""
         import numpy as np
         import torch
         self.torch = torch
@@ -25,6 +34,8 @@ class Evaluator:
             self.scene = scene
         else:
             self.scene = B.DeviceScene(scene, device)
+            if grid_cells == "auto":
+                grid_cells = auto_grid_cells(self.scene.c.n_cuboids)
             if grid_cells:
                 reach = float(np.max(self.robot.host.sphere_local[:, 3]))
                 self.scene.build_grid(reach, params.eta, grid_cells)

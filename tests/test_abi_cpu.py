@@ -249,3 +249,11 @@ def test_scene_grid_bytes_and_checks():
     sc_bad = B.vapr_scene(8, 0, 256, 256, 4104)
     assert lib.vapr_collision_cost(byref(r), byref(sc_bad), byref(p), 256, 4, byref(t),
                                    None, None, None, None) == 3
+
+
+def test_auto_grid_cells():
+    from paper_2310_07854_gb300.path import auto_grid_cells
+    assert auto_grid_cells(40) == 128                 # 17 MB
+    assert auto_grid_cells(0) == 128
+    c = auto_grid_cells(1024)                         # 32 words per cell
+    assert B.vapr_scene_grid_bytes(1024, c) <= 32 << 20 < B.vapr_scene_grid_bytes(1024, c + 8)
