@@ -204,7 +204,13 @@ vapr_status vapr_fk(const vapr_robot* robot, const float* q, int64_t n,
  * table->dist.  grad_packed: NULL or [n] rows of S*3 values of dC/dc_s in
  * table->grad.  The environment sum runs over every cuboid; the hinge's
  * gradient at exactly zero penetration is 0, and a self pair at zero
- * distance adds no gradient. */
+ * distance adds no gradient.  Each configuration's outputs depend on that
+ * configuration alone (fixed summation orders), whatever the batch, the
+ * scene grid or the order in which the kernel's warps take configurations;
+ * launches on different streams, and replays of captured launches, may
+ * overlap.  The call keeps a small host-side record per device for the
+ * kernel's work counters (an event per recent launch); it allocates no
+ * device memory. */
 vapr_status vapr_collision_cost(const vapr_robot* robot, const vapr_scene* scene,
                                 const vapr_cost_params* params,
                                 const void* pos_packed, int64_t n,
