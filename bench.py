@@ -56,7 +56,8 @@ def parse_args():
                     help="skip the learned-surrogate leg (training + gated collision)")
     ap.add_argument("--surrogate-epochs", type=int, default=80)
     ap.add_argument("--no-search", action="store_true", help="skip the VaPr format search leg")
-    ap.add_argument("--kernel", choices=["fk", "collision", "backward", "mlp_infer", "step"], default=None,
+    ap.add_argument("--kernel", choices=["fk", "collision", "backward", "mlp_infer", "step", "ceiling"],
+                    default=None,
                     help="profiling mode: run only this stage (--warmup launches, then --steps timed) on "
                          "--configs configurations of the workload and print its CUDA-event time")
     ap.add_argument("--search-samples", type=int, default=300)
@@ -299,6 +300,64 @@ def broad_phase_leg(w, ev32, q, n, args, flush, torch):
 def fp32_peak_tflops(peaks) -> float:
     """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x max SM clock."""
     return 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def ceiling_leg(w, ev32, q, n, flush, torch, peak_alu, reps=64, rounds=10):
+    """Measured compute ceiling of the collision stage's pair test
+    (vapr_env_ceiling): the stage's own environment loop in registers on the
+    workload's FP32 sphere centres moved 100 m away, so that every
+    sphere/cuboid pair runs its bounding test (10 FLOP) and none passes;
+    64 spheres x every resident warp x 4, `reps` repetitions per launch, L2
+    flushed before each timed launch.  Also times the same loop on the real
+    centres (bounding tests plus the exact distances that pass, no broad
+    phase, no memory): the in-register cost of the plain environment term
+    per configuration."""
+    from paper_2310_07854_gb300 import binding as B
+    S, O = w.robot.n_spheres, w.scene.n_cuboids
+    ev32.fk(q, n)
+    cen = ev32.pos.view(torch.float32)[:n, :3 * S].reshape(n * S, 3)
+    rad = torch.as_tensor(np.asarray(w.robot.sphere_local, np.float32)[:, 3], device="cuda").repeat(n)
+    sph = torch.cat([cen, rad[:, None]], dim=1)
+    W = B.vapr_env_ceiling_warps(O)
+    if W <= 0:
+        raise RuntimeError("vapr_env_ceiling_warps: no resident warps")
+    nc = 64 * W * 4
+    tiled = sph[torch.arange(nc, device="cuda") % sph.shape[0]].contiguous()
+    far = tiled.clone()
+    far[:, 0] += 100.0
+    out = torch.empty_like(tiled)
+
+    def timed(spheres, r):
+        for _ in range(3):
+            B.vapr_env_ceiling(ev32.scene, spheres, nc, w.params.eta, w.params.w_coll, r, out)
+        ts = []
+        for _ in range(rounds):
+            flush.add_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            B.vapr_env_ceiling(ev32.scene, spheres, nc, w.params.eta, w.params.w_coll, r, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts)
+
+    ms = timed(far, reps)
+    if int(torch.count_nonzero(out)) != 0:
+        raise RuntimeError("vapr_env_ceiling: spheres 100 m away reported contact")
+    tests_per_s = nc * O * reps / (ms / 1000.0)
+    tflops = 10 * tests_per_s / 1e12
+    ms_w = timed(tiled, reps // 8)
+    return {"tflops": tflops, "bounding_tests_per_s": tests_per_s,
+            "frac_of_derived_peak": tflops / peak_alu, "ms_per_launch": ms,
+            "spheres": nc, "cuboids": O, "reps": reps, "resident_warps": W,
+            "loop": "vapr_env_ceiling: the collision stage's environment loop (bounding test, exact box "
+                    "term where it passes, 2 spheres per lane, cuboids in shared memory) on centres "
+                    "held in registers; all spheres 100 m from the scene, so every pair runs the "
+                    "10-FLOP bounding test and none passes",
+            "plain_env_term_in_registers": {
+                "ns_per_config": ms_w * 1e6 / (nc * (reps // 8)) * S,
+                "note": "the same loop on the workload's real centres: bounding tests plus the exact "
+                        "distances that pass, no scene grid, no packed rows"}}
 
 
 def search_leg(w, ev32, q, n, args, flush, torch, per32):
@@ -582,6 +641,14 @@ def kernel_mode(args):
     n = args.configs or w.n
     q = torch.as_tensor(synth.make_q(500, n), device="cuda")
     table = F.FormatTable.parse(args.table) if args.table != "fp32" else F.FP32_TABLE
+    if args.kernel == "ceiling":
+        ev = Evaluator(w.robot, w.scene, w.params, n, F.FP32_TABLE)
+        l2 = torch.cuda.get_device_properties(0).L2_cache_size
+        flush = torch.zeros(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+        res = ceiling_leg(w, ev, q, n, flush, torch, fp32_peak_tflops(measured_peaks()[0]))
+        print(json.dumps({"kernel": "ceiling", "workload": args.workload, **res,
+                          "device_error": B.vapr_device_error()}))
+        return
     if args.kernel == "mlp_infer":
         st = B.alloc_mlp_state()
         B.vapr_mlp_init(st, torch.as_tensor(synth.init_mlp_params(5), device="cuda"))
@@ -709,6 +776,12 @@ def main():
                 "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_source": peak_kind,
                 "traffic": None if traffic is None else traffic * n,
                 "algorithmic_bytes_per_launch": bpc[dom] * n}
+    if dom == "collision":
+        ceil = ceiling_leg(w, ev32, q, n, flush, torch, roof["peak"])
+        roof["measured_ceiling"] = {"tflops": ceil["tflops"], "frac": ach / ceil["tflops"],
+                                    "source": "vapr_env_ceiling (see alu_ceiling)"}
+    else:
+        ceil = None
     stages = {}
     for ev_, per_, name in ((ev32, per32, "fp32"), (evv, perv, "vapr")):
         bp = ev_.bytes_per_config()
@@ -794,6 +867,7 @@ def main():
                      "speedup_vs_fp32": value_v / value, "ms_per_step": tv / args.steps,
                      "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale},
             "stages": stages,
+            "alu_ceiling": ceil,
             "broad_phase": broad,
             "fused_single_launch": fused,
             "swept": swept,

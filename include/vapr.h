@@ -254,6 +254,34 @@ vapr_status vapr_swept_cost(const vapr_robot* robot, const vapr_scene* scene,
                             int32_t horizon, int32_t samples, const vapr_format_table* table,
                             float* cost, void* dist_packed, void* grad_packed, void* stream);
 
+/* ---- compute ceiling of the environment pair test (measurement) ---------- */
+/* The collision stage is bound by FP32 arithmetic, not by memory, so its
+ * roofline needs a compute ceiling; this call measures one.  The paper has
+ * no counterpart: it is a measurement aid of this library.
+ * It runs the collision stage's own environment loop (Sec. III-B step 3:
+ * per sphere and cuboid, the bounding-sphere test, then the exact box term
+ * where it passes, two spheres per lane, cuboids in shared memory) on
+ * sphere centres held in registers, repeating it `reps` times per group of
+ * 64 spheres, with no packed rows, no self pairs and no scene grid.  On
+ * spheres that clear every cuboid the loop is the bounding tests alone, so
+ * n * n_cuboids * reps / time is the GPU's rate of the method's pair tests.
+ *  - spheres: float32 [n][4] (x, y, z, r), device, 16-byte aligned.
+ *  - out: float32 [n][4], device, 16-byte aligned: per sphere the
+ *    environment term of vapr_collision_cost with these margins,
+ *    (D_s = sum_o max(0, r + eta - d_o(c)), G_s = w_coll dD_s/dc), from the
+ *    last repetition (every repetition computes the same values).
+ *  - reps >= 1; n = 0 does nothing.  scene->grid is ignored.
+ *  - Errors: INVALID_ARG (NULL pointers, n < 0, reps < 1), MISALIGNED,
+ *    TOO_LARGE (n_cuboids), CUDA.  Asynchronous on the stream. */
+vapr_status vapr_env_ceiling(const vapr_scene* scene, const float* spheres, int64_t n,
+                             float eta, float w_coll, int32_t reps, float* out, void* stream);
+
+/* Warps one vapr_env_ceiling launch keeps resident on the current device
+ * for a scene of n_cuboids (every SM full); each warp takes 64 spheres at a
+ * time, so n a multiple of 64 times this count gives every warp the same
+ * work.  0 on error (no device, n_cuboids out of range). */
+int64_t vapr_env_ceiling_warps(int32_t n_cuboids);
+
 /* ---- IK optimisation iteration (Sec. III-B, iteration steps 1-7) --------- */
 /* A batch of IK seeds optimised on the GPU around the cost-and-gradient
  * path.  Each iteration (vapr_ik_step) evaluates every seed at N step

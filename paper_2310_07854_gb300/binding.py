@@ -145,6 +145,9 @@ SIGNATURES = {
                                        ctypes.POINTER(vapr_cost_params), _P, _i64, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.POINTER(vapr_format_table), _P, _P, _P,
                                        _P]),
+    "vapr_env_ceiling": (ctypes.c_int, [ctypes.POINTER(vapr_scene), _P, _i64, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_int32, _P, _P]),
+    "vapr_env_ceiling_warps": (ctypes.c_int64, [ctypes.c_int32]),
     "vapr_ik_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(vapr_robot), _i64,
                                                   ctypes.POINTER(vapr_ik_params),
                                                   ctypes.POINTER(vapr_format_table)]),
@@ -374,6 +377,16 @@ def vapr_swept_cost(robot: DeviceRobot, scene: DeviceScene, params, pos_packed, 
                                    _ptr(pos_packed), n, horizon, samples, ctypes.byref(ct), _ptr(cost),
                                    _ptr(dist_packed), _ptr(grad_packed), _stream(stream)),
            "vapr_swept_cost")
+
+
+def vapr_env_ceiling(scene: DeviceScene, spheres, n, eta, w_coll, reps, out, stream=None):
+    """spheres, out: float32 [n, 4] device tensors (x, y, z, r) -> (D, G)."""
+    _check(_load().vapr_env_ceiling(ctypes.byref(scene.c), _ptr(spheres), n, eta, w_coll, reps,
+                                    _ptr(out), _stream(stream)), "vapr_env_ceiling")
+
+
+def vapr_env_ceiling_warps(n_cuboids: int) -> int:
+    return int(_load().vapr_env_ceiling_warps(n_cuboids))
 
 
 def vapr_backward(robot: DeviceRobot, q, xform_packed, grad_packed, dcost, n,

@@ -257,3 +257,23 @@ def test_auto_grid_cells():
     assert auto_grid_cells(0) == 128
     c = auto_grid_cells(1024)                         # 32 words per cell
     assert B.vapr_scene_grid_bytes(1024, c) <= 32 << 20 < B.vapr_scene_grid_bytes(1024, c + 8)
+
+
+def test_env_ceiling_argument_checks():
+    """The pair-test ceiling rejects bad arguments before touching a device."""
+    lib = B.lib()
+    scene = B.vapr_scene(2, 0, 4096, 8192)
+    call = lambda n, reps=4, sp=4096, out=8192, sc=ctypes.byref(scene): lib.vapr_env_ceiling(
+        sc, sp, n, 0.02, 1.0, reps, out, None)
+    assert call(0) == 0                  # nothing to do
+    assert call(-1) == 1
+    assert call(64, reps=0) == 1
+    assert call(64, sp=None) == 1
+    assert call(64, out=None) == 1
+    assert call(64, sp=4100) == 3        # spheres not 16-byte aligned
+    assert call(64, out=8200) == 3
+    assert call(64, sc=None) == 1
+    big = B.vapr_scene(B.MAX_CUBOIDS + 1, 0, 4096, 8192)
+    assert call(64, sc=ctypes.byref(big)) == 6
+    assert lib.vapr_env_ceiling_warps(-1) == 0
+    assert lib.vapr_env_ceiling_warps(B.MAX_CUBOIDS + 1) == 0
