@@ -374,7 +374,7 @@ void or_collision(int ns, const float* sphere_local, int npairs,
         d2 += diff[k] * diff[k];
       }
       double dd = sqrt(d2);
-      double pen = sphere_local[4 * i + 3] + sphere_local[4 * j + 3] + eta_s - dd;
+      double pen = (double)sphere_local[4 * i + 3] + (double)sphere_local[4 * j + 3] + eta_s - dd;
       if (K && (fabs(pen) < kink_eps || (pen > 0.0 && dd < kink_eps))) K[i] = K[j] = 1;
       if (pen > 0.0) {
         total += w_s * pen;

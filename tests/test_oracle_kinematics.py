@@ -142,6 +142,32 @@ def test_self_collision_closed_form(orc):
     assert np.all(col["dist"] == 0)
 
 
+def test_cost_weights_scale_their_terms(orc):
+    """Sphere 0 is 3 cm outside the -x face of an axis-aligned box and in
+    the one non-adjacent pair (0, 2); weights w_coll = 0.7, w_self = 1.9:
+    C = w_coll (r_0 + eta - 0.03) + w_self (r_0 + r_2 + eta_s - |c_0 - c_2|),
+    D is the unweighted penetration, and each term's gradient carries its
+    own weight (environment: -w_coll e_x on sphere 0)."""
+    robot = _robot([_tf()] * 3, [[0, 0, 0, 0.05], [0, 0, 0, 0.05], [0, 0, 0, 0.04]],
+                   [1, 2, 3])
+    hx = 0.2
+    scene = _scene([(np.eye(3), (-0.03 - hx, 0.0, 0.0), (hx, 0.05, 0.05))])
+    pos = np.array([[[0, 0, 0], [0.05, 0, 0], [0.06, 0.02, 0.0]]])
+    params = synth.CostParams(eta=0.02, eta_self=0.01, w_coll=0.7, w_self=1.9)
+    col = orc.collision(robot, scene, params, pos)
+    r0, r2 = float(np.float32(0.05)), float(np.float32(0.04))
+    dist = np.hypot(0.06, 0.02)
+    face = float(np.float32(-0.03 - hx)) + float(np.float32(hx))  # the -x face as stored
+    pen_env = r0 + 0.02 + face  # d = -face: sphere 0 sits at the origin
+    pen_self = r0 + r2 + 0.01 - dist
+    assert col["dist"][0] == pytest.approx([pen_env, 0.0, 0.0], abs=1e-9)
+    assert col["cost"][0] == pytest.approx(0.7 * pen_env + 1.9 * pen_self, rel=1e-9)
+    u = np.array([0.06, 0.02, 0.0]) / dist
+    assert np.allclose(col["grad"][0, 0], [-0.7, 0.0, 0.0] + 1.9 * u, atol=1e-9)
+    assert np.allclose(col["grad"][0, 1], 0.0)
+    assert np.allclose(col["grad"][0, 2], -1.9 * u, atol=1e-9)
+
+
 # ------------------------------------------------------- finite differences
 def test_gradient_wrt_sphere_centres_fd(orc):
     w = synth.make_workload("single_128")
