@@ -91,6 +91,22 @@ def test_box_sdf_special_cases(orc):
     assert np.allclose(g_r, g @ Rz.T, atol=1e-15)
 
 
+def _box_surface(h, step):
+    """Points on the six faces of a box of half extents h (its own frame),
+    on a grid of the given spacing that includes the edges."""
+    faces = []
+    for k in range(3):
+        a, b = [j for j in range(3) if j != k]
+        ua = np.arange(-h[a], h[a] + 1e-12, step)
+        ub = np.arange(-h[b], h[b] + 1e-12, step)
+        A, B = np.meshgrid(np.append(ua, h[a]), np.append(ub, h[b]))
+        for sgn in (-1, 1):
+            P = np.zeros((A.size, 3))
+            P[:, a], P[:, b], P[:, k] = A.ravel(), B.ravel(), sgn * h[k]
+            faces.append(P)
+    return np.concatenate(faces)
+
+
 def test_box_sdf_brute_force_sampling(orc):
     """|d| equals the distance to a dense sample of the surface (within the
     grid's half-diagonal) and its sign is the containment test."""
@@ -101,17 +117,7 @@ def test_box_sdf_brute_force_sampling(orc):
         t = scene.pose[o, 9:].astype(float)
         h = scene.half_ext[o].astype(float)
         step = 0.004
-        faces = []
-        for k in range(3):
-            a, b = [j for j in range(3) if j != k]
-            ua = np.arange(-h[a], h[a] + 1e-12, step)
-            ub = np.arange(-h[b], h[b] + 1e-12, step)
-            A, B = np.meshgrid(np.append(ua, h[a]), np.append(ub, h[b]))
-            for sgn in (-1, 1):
-                P = np.zeros((A.size, 3))
-                P[:, a], P[:, b], P[:, k] = A.ravel(), B.ravel(), sgn * h[k]
-                faces.append(P)
-        surf = np.concatenate(faces)
+        surf = _box_surface(h, step)
         local = rng.uniform(-1.6, 1.6, (200, 3)) * h
         world = local @ R.T + t
         d, _ = orc.box_sdf(np.repeat(scene.pose[o:o + 1], 200, 0),
@@ -121,6 +127,49 @@ def test_box_sdf_brute_force_sampling(orc):
         tol = step * np.sqrt(2) / 2 + 1e-6
         assert np.all(np.abs(np.abs(d) - near) <= tol)
         assert np.all((d <= 1e-12) == inside)
+
+
+def test_scene_sdf_brute_force(orc):
+    """The scene distance (the surrogate's training label, the least box
+    distance over the cuboids): outside every cuboid it is the distance to
+    the nearest sampled surface point of any cuboid, inside exactly one it
+    is minus the distance to that cuboid's surface; a one-cuboid scene gives
+    the box distance itself."""
+    rng = np.random.default_rng(9)
+    scene = synth.make_scene(11, 4, extent=0.4)
+    O = scene.n_cuboids
+    Rs = scene.pose[:, :9].reshape(O, 3, 3).astype(float)
+    ts = scene.pose[:, 9:].astype(float)
+    hs = scene.half_ext.astype(float)
+    # half the points anywhere around the scene, half near a chosen cuboid
+    pick = rng.integers(0, O, 150)
+    near_box = np.einsum("nij,nj->ni", Rs[pick], rng.uniform(-1.2, 1.2, (150, 3)) * hs[pick]) + ts[pick]
+    pts = np.concatenate([rng.uniform(-0.9, 0.9, (150, 3)), near_box])
+    sdf = orc.scene_sdf(scene, pts)
+    step = 0.006
+    near = np.empty((O, len(pts)))
+    inside = np.zeros((O, len(pts)), bool)
+    for o in range(O):
+        surf = _box_surface(hs[o], step)
+        local = (pts - ts[o]) @ Rs[o]  # R^T (p - t) for each point
+        for c in range(0, len(pts), 50):
+            diff = local[c:c + 50, None, :] - surf[None]
+            near[o, c:c + 50] = np.sqrt((diff ** 2).sum(-1)).min(1)
+        inside[o] = np.all(np.abs(local) <= hs[o], axis=1)
+    tol = step * np.sqrt(2) / 2 + 1e-6
+    out = ~inside.any(0)
+    assert out.sum() > 100
+    assert np.all(sdf[out] > 0)
+    assert np.all(np.abs(sdf[out] - near[:, out].min(0)) <= tol)
+    one = inside.sum(0) == 1
+    assert one.sum() > 20
+    own = np.argmax(inside, 0)
+    assert np.all(sdf[one] <= 0)
+    assert np.all(np.abs(-sdf[one] - near[own[one], one]) <= tol)
+    single = synth.Scene(scene.pose[:1].copy(), scene.half_ext[:1].copy())
+    d, _ = orc.box_sdf(np.repeat(scene.pose[:1], len(pts), 0), np.repeat(scene.half_ext[:1], len(pts), 0),
+                       pts)
+    assert np.array_equal(orc.scene_sdf(single, pts), d)
 
 
 def test_self_collision_closed_form(orc):

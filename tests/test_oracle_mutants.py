@@ -74,6 +74,13 @@ MUTANTS = [
      "for (int k = 0; k < 3; ++k) G[3 * s + k] = gs[k];"),
     ("collision weight dropped from the cost", ["kin"],
      "total += w_c * Ds;\n      if (K) K[s] = flag;", "total += Ds;\n      if (K) K[s] = flag;"),
+    ("scene distance starts from zero", ["kin"],
+     "double best = INFINITY, g[3], margin;", "double best = 0.0, g[3], margin;"),
+    ("scene distance skips the last cuboid", ["kin"],
+     "      double d = box_sdf(pose + 12 * o, half + 3 * o, pts + 3 * i, g, &margin);\n"
+     "      if (d < best) best = d;",
+     "      double d = box_sdf(pose + 12 * o, half + 3 * o, pts + 3 * i, g, &margin);\n"
+     "      if (d < best && o + 1 < no) best = d;"),
     # self-collision (Sec. III-C out_vec)
     ("self radius of one sphere dropped", ["kin"],
      "(double)sphere_local[4 * i + 3] + (double)sphere_local[4 * j + 3] + eta_s - dd",
