@@ -9,7 +9,11 @@ shuffles the training set and picks the learning rate of each step.
 """
 from __future__ import annotations
 
+import hashlib
+import json
 import math
+import os
+import struct
 
 import numpy as np
 
@@ -39,6 +43,48 @@ def domain_box(scene: synth.Scene, pad: float = PAD):
     lo32 = np.nextafter(lo.astype(np.float32), np.float32(-np.inf))
     hi32 = np.nextafter(hi.astype(np.float32), np.float32(np.inf))
     return lo32, hi32
+
+
+# ------------------------------------------------------------ checkpoints
+# A checkpoint file: the 8-byte magic, a little-endian uint32 header length,
+# a JSON header, then the network state's raw bytes as the library keeps
+# them (master parameters, Adam moments and step, bfloat16 copies).
+CHECKPOINT_MAGIC = b"VAPRMLP1"
+
+
+def scene_hash(scene: synth.Scene) -> str:
+    """SHA-256 of the cuboid poses and half extents (float32 bytes)."""
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(scene.pose, np.float32).tobytes())
+    h.update(np.ascontiguousarray(scene.half_ext, np.float32).tobytes())
+    return h.hexdigest()
+
+
+def write_checkpoint(path: str, state: bytes, meta: dict) -> None:
+    """Writes meta (JSON) and the raw state bytes; meta gains state_bytes."""
+    header = json.dumps({**meta, "state_bytes": len(state)}, sort_keys=True).encode()
+    tmp = f"{path}.tmp"
+    with open(tmp, "wb") as f:
+        f.write(CHECKPOINT_MAGIC)
+        f.write(struct.pack("<I", len(header)))
+        f.write(header)
+        f.write(state)
+    os.replace(tmp, path)
+
+
+def read_checkpoint(path: str) -> tuple[dict, bytes]:
+    """(meta, state bytes) of a checkpoint file; ValueError if it is not one
+    or is cut short."""
+    with open(path, "rb") as f:
+        data = f.read()
+    if data[:8] != CHECKPOINT_MAGIC or len(data) < 12:
+        raise ValueError(f"{path}: not a surrogate checkpoint")
+    (hl,) = struct.unpack("<I", data[8:12])
+    meta = json.loads(data[12:12 + hl].decode())
+    state = data[12 + hl:]
+    if len(state) != meta.get("state_bytes"):
+        raise ValueError(f"{path}: {len(state)} state bytes, header says {meta.get('state_bytes')}")
+    return meta, state
 
 
 class Surrogate:
@@ -142,6 +188,37 @@ class Surrogate:
         p = torch.empty(B.MLP_PARAMS, dtype=torch.float32, device=self.device)
         B.vapr_mlp_get_params(self.state, p)
         return p
+
+    # -------------------------------------------------------- checkpoints
+    def meta(self) -> dict:
+        return {"format": 1, "hidden": B.MLP_HIDDEN, "params": B.MLP_PARAMS,
+                "scene_sha256": scene_hash(self.scene.host),
+                "lo": [float(v) for v in self.lo], "hi": [float(v) for v in self.hi],
+                "pad": float(self.domain.pad), "margin": float(self.domain.margin)}
+
+    def save(self, path: str, **extra) -> None:
+        """Writes the whole network state (weights, Adam moments and step)
+        and the gate domain; `extra` (seed, epochs, ...) goes into the
+        header.  The copy to the host waits for the state's pending updates
+        on the current stream."""
+        write_checkpoint(path, self.state.cpu().numpy().tobytes(), {**extra, **self.meta()})
+
+    def load(self, path: str) -> dict:
+        """Restores a state saved by `save` for this scene (same cuboids,
+        same library state layout) and its gate margin; training resumes
+        where it stopped.  Returns the header."""
+        import torch
+        meta, state = read_checkpoint(path)
+        mine = self.meta()
+        for key in ("format", "hidden", "params", "scene_sha256", "lo", "hi", "pad"):
+            if meta.get(key) != mine[key]:
+                raise ValueError(f"{path}: {key} {meta.get(key)!r} does not match this surrogate's {mine[key]!r}")
+        if len(state) != self.state.numel():
+            raise ValueError(f"{path}: {len(state)} state bytes, this library keeps {self.state.numel()}")
+        host = torch.frombuffer(bytearray(state), dtype=torch.uint8)
+        self.state.copy_(host.to(self.state.device))
+        self.domain.margin = float(meta["margin"])
+        return meta
 
     def collision_cost(self, robot: B.DeviceRobot, params, pos_packed, n, table, cost=None,
                        dist_packed=None, grad_packed=None, estimate=None, stream=None):
