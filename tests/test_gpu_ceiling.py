@@ -106,9 +106,9 @@ def test_bench_launch_configuration():
     tiled = sph[np.arange(nc) % sph.shape[0]]
     far = tiled.copy()
     far[:, 0] += 100.0
-    out = _ceiling(sd, far, w.params.eta, w.params.w_coll, 64)
+    out = _ceiling(sd, far, w.params.eta, w.params.w_coll, 16)
     assert torch.count_nonzero(out) == 0
-    out = _ceiling(sd, tiled, w.params.eta, w.params.w_coll, 8).cpu().numpy().astype(np.float64)
+    out = _ceiling(sd, tiled, w.params.eta, w.params.w_coll, 2).cpu().numpy().astype(np.float64)
     idx = np.random.default_rng(3).choice(nc, 2000, replace=False)
     src = idx % sph.shape[0]
     cfg, s = src // robot.n_spheres, src % robot.n_spheres
