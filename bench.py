@@ -61,6 +61,8 @@ def parse_args():
                     help="profiling mode: run only this stage (--warmup launches, then --steps timed) on "
                          "--configs configurations of the workload and print its CUDA-event time")
     ap.add_argument("--search-samples", type=int, default=300)
+    ap.add_argument("--ceiling-reps", type=int, default=16,
+                    help="repetitions per launch of the pair-test ceiling measurement")
     ap.add_argument("--configs", type=int, default=0,
                     help="override the batch size (configurations per GPU)")
     return ap.parse_args()
@@ -311,7 +313,7 @@ def ceiling_leg(w, ev32, q, n, flush, torch, peak_alu, reps=16, rounds=5):
     flushed before each timed launch.  Also times the same loop on the real
     centres (bounding tests plus the exact distances that pass, no broad
     phase, no memory): the in-register cost of the plain environment term
-    per configuration.  About 4 ms of GPU time in all, so that this
+    per configuration.  About 5 ms of GPU time in all, so that this
     measurement stays a small share of a bench run's launches."""
     from paper_2310_07854_gb300 import binding as B
     S, O = w.robot.n_spheres, w.scene.n_cuboids
@@ -329,7 +331,7 @@ def ceiling_leg(w, ev32, q, n, flush, torch, peak_alu, reps=16, rounds=5):
     out = torch.empty_like(tiled)
 
     def timed(spheres, r):
-        for _ in range(2):
+        for _ in range(3):
             B.vapr_env_ceiling(ev32.scene, spheres, nc, w.params.eta, w.params.w_coll, r, out)
         ts = []
         for _ in range(rounds):
@@ -647,7 +649,8 @@ def kernel_mode(args):
         ev = Evaluator(w.robot, w.scene, w.params, n, F.FP32_TABLE)
         l2 = torch.cuda.get_device_properties(0).L2_cache_size
         flush = torch.zeros(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
-        res = ceiling_leg(w, ev, q, n, flush, torch, fp32_peak_tflops(measured_peaks()[0]))
+        res = ceiling_leg(w, ev, q, n, flush, torch, fp32_peak_tflops(measured_peaks()[0]),
+                          reps=args.ceiling_reps)
         print(json.dumps({"kernel": "ceiling", "workload": args.workload, **res,
                           "device_error": B.vapr_device_error()}))
         return
@@ -779,7 +782,7 @@ def main():
                 "traffic": None if traffic is None else traffic * n,
                 "algorithmic_bytes_per_launch": bpc[dom] * n}
     if dom == "collision":
-        ceil = ceiling_leg(w, ev32, q, n, flush, torch, roof["peak"])
+        ceil = ceiling_leg(w, ev32, q, n, flush, torch, roof["peak"], reps=args.ceiling_reps)
         roof["measured_ceiling"] = {"tflops": ceil["tflops"], "frac": ach / ceil["tflops"],
                                     "source": "vapr_env_ceiling (see alu_ceiling)"}
     else:
