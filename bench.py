@@ -299,6 +299,16 @@ def broad_phase_leg(w, ev32, q, n, args, flush, torch):
                              "collision_ms": statistics.mean(per["collision"])}}
 
 
+def sparsity(dist, grad, S: int) -> dict:
+    """Fraction of nonzero per-sphere penetrations D and of spheres with a
+    nonzero gradient G (the zero words the backward pass skips); dist
+    [n, S] and grad [n, 3S] decoded float tensors."""
+    n = dist.shape[0]
+    g = grad[:, :3 * S].reshape(n, S, 3)
+    return {"dist_nonzero": float((dist[:, :S] != 0).float().mean()),
+            "grad_spheres_nonzero": float((g != 0).any(-1).float().mean())}
+
+
 def fp32_peak_tflops(peaks) -> float:
     """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x max SM clock."""
     return 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
@@ -756,6 +766,7 @@ def main():
     a, b = decoded(ev32), decoded(evv)
     err = {k: float((a[k] - b[k]).abs().max()) for k in a}
     err_scale = {k: float(a[k].abs().max()) for k in a}
+    sparse = sparsity(a["dist"], a["grad"], w.robot.n_spheres)
 
     # roofline of the dominant kernel (FP32 table).  FK and backward are
     # HBM-bound stages; the collision stage is bound by FP32 ALU work (every
@@ -872,6 +883,7 @@ def main():
                      "speedup_vs_fp32": value_v / value, "ms_per_step": tv / args.steps,
                      "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale},
             "stages": stages,
+            "sparsity": sparse,
             "alu_ceiling": ceil,
             "broad_phase": broad,
             "fused_single_launch": fused,
