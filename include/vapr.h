@@ -26,7 +26,8 @@
  *    pair indices) cannot be checked without a copy: kernels clamp them into
  *    range so no access leaves its buffer; vapr_robot_check() validates
  *    them once, synchronously, at set-up.
- *  - n == 0 is a no-op returning VAPR_OK.
+ *  - n == 0 is a no-op returning VAPR_OK; a configuration count above
+ *    VAPR_MAX_CONFIGS returns VAPR_ERR_TOO_LARGE.
  *  - Packed layout: row r of a packed tensor starts at byte
  *    r * vapr_packed_row_bytes(row_len, fmt).  Value i of a row sits in
  *    32-bit little-endian word i / k, bits [b*(i%k), b*(i%k)+b) with
@@ -64,6 +65,11 @@ typedef enum {
 #define VAPR_MAX_SPHERES 128
 #define VAPR_MAX_PAIRS 8128   /* all pairs of 128 spheres */
 #define VAPR_MAX_CUBOIDS 1024
+/* Configurations per call of any entry point that takes a configuration
+ * count n (per problem for vapr_batched_*); larger n returns
+ * VAPR_ERR_TOO_LARGE.  2^31 configurations of the smallest packed formats
+ * already take over 170 GB. */
+#define VAPR_MAX_CONFIGS ((int64_t)1 << 31)
 
 /* Format flags (Sec. IV-A gives only bit counts; these classes are the
  * reading that agrees with IEEE half/bfloat16 and the OCP 8/6/4-bit types):

@@ -345,6 +345,7 @@ vapr_status vapr_fk(const vapr_robot* robot, const float* q, int64_t n,
   if (st != VAPR_OK) return st;
   if ((st = check_table(table)) != VAPR_OK) return st;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
   if (n == 0) return VAPR_OK;
   if (!q || !pos_packed) return VAPR_ERR_INVALID_ARG;
   if (!aligned(q, 4) || !aligned(pos_packed, 16) || (xform_packed && !aligned(xform_packed, 16)))
@@ -366,6 +367,7 @@ vapr_status vapr_collision_cost(const vapr_robot* robot, const vapr_scene* scene
   SceneArgs sc;
   if ((st = check_scene(scene, &sc)) != VAPR_OK) return st;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
   if (n == 0) return VAPR_OK;
   if (!pos_packed) return VAPR_ERR_INVALID_ARG;
   if (!aligned(pos_packed, 16) || (cost && !aligned(cost, 4)) ||
@@ -382,7 +384,9 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t vapr_cost_grad_workspace_bytes(const vapr_robot* robot, int64_t n,
                                       const vapr_format_table* table) {
   RobotArgs r;
-  if (check_robot(robot, &r) != VAPR_OK || check_table(table) != VAPR_OK || n < 0) return 0;
+  if (check_robot(robot, &r) != VAPR_OK || check_table(table) != VAPR_OK || n < 0 ||
+      n > VAPR_MAX_CONFIGS)
+    return 0;
   const size_t P = row_bytes(3 * (int64_t)r.S, table->pos) * (size_t)n;
   const size_t G = row_bytes(3 * (int64_t)r.S, table->grad) * (size_t)n;
   return align256(P) + align256(G);
@@ -401,6 +405,7 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
   SceneArgs sc;
   if ((st = check_scene(scene, &sc)) != VAPR_OK) return st;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
   if (n == 0) return VAPR_OK;
   if (!q || !cost || !jgrad_packed || !workspace) return VAPR_ERR_INVALID_ARG;
   if (workspace_bytes < vapr_cost_grad_workspace_bytes(robot, n, table)) return VAPR_ERR_INVALID_ARG;
@@ -429,6 +434,7 @@ vapr_status vapr_backward(const vapr_robot* robot, const float* q, const void* x
   if (st != VAPR_OK) return st;
   if ((st = check_table(table)) != VAPR_OK) return st;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
   if (n == 0) return VAPR_OK;
   if (!grad_packed || !jgrad_packed || (!q && !xform_packed)) return VAPR_ERR_INVALID_ARG;
   if ((q && !aligned(q, 4)) || !aligned(grad_packed, 16) || !aligned(jgrad_packed, 16) ||

@@ -257,7 +257,7 @@ static vapr_status layout(const vapr_problem* pr, int32_t np, const vapr_format_
     if ((st = check_robot(&p.robot, &d.r)) != VAPR_OK) return st;
     if (p.scene.n_cuboids < 0 || p.n < 0 || p.reserved != 0 || (p.deferred != 0 && p.deferred != 1))
       return VAPR_ERR_INVALID_ARG;
-    if (p.scene.n_cuboids > VAPR_MAX_CUBOIDS) return VAPR_ERR_TOO_LARGE;
+    if (p.scene.n_cuboids > VAPR_MAX_CUBOIDS || p.n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
     if (p.scene.n_cuboids > 0 && (!p.scene.pose || !p.scene.half_ext)) return VAPR_ERR_INVALID_ARG;
     if (p.n > 0 && (!p.q || !p.cost || !p.jgrad_packed)) return VAPR_ERR_INVALID_ARG;
     if ((p.scene.n_cuboids > 0 && (!al(p.scene.pose, 16) || !al(p.scene.half_ext, 4))) ||

@@ -314,6 +314,7 @@ static vapr_status check_ik(const vapr_robot* robot, const vapr_scene* scene, co
       ik->history > VAPR_IK_MAX_HISTORY || !(ik->step0 > 0.f) || !ik->q_lo || !ik->q_hi)
     return VAPR_ERR_INVALID_ARG;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
   if (n > 0 && (!goal || !q)) return VAPR_ERR_INVALID_ARG;
   if ((uintptr_t)goal % 4 || (uintptr_t)q % 4) return VAPR_ERR_MISALIGNED;
   return VAPR_OK;

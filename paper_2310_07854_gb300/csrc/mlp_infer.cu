@@ -451,6 +451,7 @@ extern "C" vapr_status vapr_surrogate_collision_cost(const vapr_robot* robot, co
   if ((v = check_domain(domain)) != VAPR_OK) return v;
   if (!params) return VAPR_ERR_INVALID_ARG;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
   if (n == 0) return VAPR_OK;
   if (!net || !pos_packed || !estimate) return VAPR_ERR_INVALID_ARG;
   if ((uintptr_t)net % 256 || (uintptr_t)estimate % 4) return VAPR_ERR_MISALIGNED;

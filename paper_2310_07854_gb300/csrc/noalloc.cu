@@ -49,10 +49,15 @@ extern "C" vapr_status vapr_cost_grad_noalloc(const vapr_robot* robot, const vap
                                               const float* dcost, float* cost,
                                               void* dist_packed, void* jgrad_packed,
                                               void* stream) {
+  vapr::RobotArgs r;
+  vapr_status st = vapr::check_robot(robot, &r);
+  if (st != VAPR_OK) return st;
+  if ((st = vapr::check_table(table)) != VAPR_OK) return st;
   if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
   if (n == 0) return VAPR_OK;
   const size_t need = vapr_cost_grad_workspace_bytes(robot, n, table);
-  if (need == 0) return robot && table ? VAPR_ERR_UNSUPPORTED_FORMAT : VAPR_ERR_INVALID_ARG;
+  if (need == 0) return VAPR_ERR_INVALID_ARG;
   if (need > (size_t)VAPR_NOALLOC_SCRATCH_BYTES) return VAPR_ERR_TOO_LARGE;
   void* scratch = nullptr;
   const cudaError_t e = vapr::scratch_address(&scratch);

@@ -231,7 +231,7 @@ extern "C" vapr_status vapr_swept_cost(const vapr_robot* robot, const vapr_scene
   SceneArgs sc;
   if ((v = check_scene(scene, &sc)) != VAPR_OK) return v;
   if (n < 0 || horizon < 1 || samples < 1) return VAPR_ERR_INVALID_ARG;
-  if (samples > VAPR_MAX_SWEPT_SAMPLES) return VAPR_ERR_TOO_LARGE;
+  if (samples > VAPR_MAX_SWEPT_SAMPLES || n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
   if (n % horizon) return VAPR_ERR_INVALID_ARG;
   if (n == 0) return VAPR_OK;
   if (!pos_packed) return VAPR_ERR_INVALID_ARG;

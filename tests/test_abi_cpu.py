@@ -277,3 +277,59 @@ def test_env_ceiling_argument_checks():
     assert call(64, sc=ctypes.byref(big)) == 6
     assert lib.vapr_env_ceiling_warps(-1) == 0
     assert lib.vapr_env_ceiling_warps(B.MAX_CUBOIDS + 1) == 0
+
+
+def test_configuration_count_limit():
+    """n above VAPR_MAX_CONFIGS (2^31) is refused before any device work,
+    by every entry point that takes a configuration count (fake device
+    addresses, never dereferenced)."""
+    lib = B.lib()
+    byref = ctypes.byref
+    big, TOO = (1 << 31) + 1, 6
+    t = B.to_c_table(F.FP32_TABLE)
+    r = _robot_struct()
+    p = B.vapr_cost_params(0.02, 0.01, 1.0, 1.0)
+    sc = B.vapr_scene(8, 0, 256, 256)
+    assert lib.vapr_fk(byref(r), 256, big, byref(t), 256, None, None) == TOO
+    assert lib.vapr_collision_cost(byref(r), byref(sc), byref(p), 256, big, byref(t),
+                                   None, None, None, None) == TOO
+    assert lib.vapr_backward(byref(r), 256, None, 256, None, big, byref(t), 256, None) == TOO
+    assert lib.vapr_cost_grad_workspace_bytes(byref(r), big, byref(t)) == 0
+    assert lib.vapr_cost_grad(byref(r), byref(sc), byref(p), 256, big, byref(t), None, 256, None,
+                              256, 256, 1 << 20, None) == TOO
+    assert lib.vapr_cost_grad_noalloc(byref(r), byref(sc), byref(p), 256, big, byref(t), None, 256,
+                                      None, 256, None) == TOO
+    assert lib.vapr_swept_cost(byref(r), byref(sc), byref(p), 256, big, 1, 4, byref(t),
+                               None, None, None, None) == TOO
+    dom = B.surrogate_domain([-1, -1, -1], [1, 1, 1], 0.1, 0.05)
+    assert lib.vapr_surrogate_collision_cost(byref(r), byref(sc), byref(p), 4096, byref(dom), 256, big,
+                                             byref(t), None, None, None, 256, None) == TOO
+    ik = B.vapr_ik_params(100.0, 10.0, 100.0, 0.2, 8, 6, (ctypes.c_float * 16)(*([0.0] * 16)), 256, 256)
+    assert lib.vapr_ik_init(byref(r), byref(sc), byref(p), byref(ik), 256, 256, big, byref(t), 256,
+                            1 << 20, 256, None) == TOO
+    arr = (B.vapr_problem * 1)()
+    arr[0].robot, arr[0].scene, arr[0].params = r, sc, p
+    arr[0].q, arr[0].cost, arr[0].jgrad_packed, arr[0].n = 256, 256, 256, big
+    plan = B.vapr_batch_plan()
+    assert lib.vapr_batched_plan(arr, 1, byref(t), byref(B.vapr_batch_tuning(128, 0)), 256, 1 << 20,
+                                 byref(plan)) == TOO
+
+
+def test_noalloc_statuses():
+    """The no-allocation step names each fault: a bad robot, a bad format
+    and a batch beyond its array each get their own status."""
+    lib = B.lib()
+    byref = ctypes.byref
+    t = B.to_c_table(F.FP32_TABLE)
+    p = B.vapr_cost_params(0.02, 0.01, 1.0, 1.0)
+    sc = B.vapr_scene(8, 0, 256, 256)
+    call = lambda robot, table, n: lib.vapr_cost_grad_noalloc(robot, byref(sc), byref(p), 256, n, table,
+                                                              None, 256, None, 256, None)
+    assert call(byref(_robot_struct(n_joints=0)), byref(t), 4) == 1
+    assert call(None, byref(t), 4) == 1
+    bad = B.to_c_table(F.FP32_TABLE)
+    bad.dist = B.vapr_format(9, 1, 4, 0)
+    assert call(byref(_robot_struct()), byref(bad), 4) == 2
+    assert call(byref(_robot_struct()), byref(t), -1) == 1
+    assert call(byref(_robot_struct()), byref(t), 0) == 0
+    assert call(byref(_robot_struct()), byref(t), 1 << 20) == 6   # beyond the 64 MiB array
