@@ -106,3 +106,62 @@ def test_iteration_never_increases_the_cost(orc):
     out = orc.ik_iterate(w.robot, w.scene, w.params, ik, goal[:32], w.q[:32], iters=4)
     assert np.all(np.diff(out["cost"], axis=0) <= 1e-12)
     assert np.mean(out["cost"][-1]) < np.mean(out["cost"][0])
+
+
+def _bfgs_direction(pairs, g):
+    """-H g with H the textbook BFGS inverse update from H0 = gamma I
+    (gamma from the newest pair), pairs oldest first."""
+    dim = g.shape[0]
+    if not pairs:
+        return -g
+    s_n, y_n = pairs[-1]
+    H = (s_n @ y_n) / (y_n @ y_n) * np.eye(dim)
+    for s, y in pairs:
+        rho = 1.0 / (y @ s)
+        V = np.eye(dim) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    return -H @ g
+
+
+def test_iteration_steps_follow_the_rules(orc):
+    """Each step of the iteration, re-derived from its outputs: the kept
+    scale is the lowest-cost candidate (costs recomputed one by one); the
+    first step and every step after keeping scale 0 follow steepest descent
+    scaled so that scale 1 moves the largest joint by step0; otherwise the
+    direction is the BFGS step from the newest `history` pairs with
+    positive curvature, and a pair without positive curvature is skipped."""
+    w = synth.make_workload("single_128")
+    ik = _ik(7)
+    ik.history = 2
+    ik.scales = [0.0, 0.1, 0.5, 2.0]  # long steps overshoot: scale 0 is kept now and then
+    n, iters = 24, 6
+    goal = _goal_from(orc, w.robot, synth.make_q(9, w.n))[:n]
+    out = orc.ik_iterate(w.robot, w.scene, w.params, ik, goal, w.q[:n], iters=iters)
+    scales = np.asarray(ik.scales)
+    restarts = curv_steps = trims = after_restart = 0
+    for i in range(n):
+        qs = out["q"][:, i]
+        g = [orc.ik_costs(w.robot, w.scene, w.params, ik, goal[i:i + 1], qs[k:k + 1].astype(np.float32))[1][0]
+             for k in range(iters + 1)]
+        d = -g[0] * ik.step0 / np.abs(g[0]).max()
+        pairs = []
+        for k in range(iters):
+            cand = (qs[k][None] + scales[:, None] * d[None]).astype(np.float32)
+            fc = orc.ik_costs(w.robot, w.scene, w.params, ik, np.repeat(goal[i:i + 1], len(scales), 0), cand)[0]
+            pick = out["pick"][k, i]
+            assert pick == np.argmin(fc)
+            assert np.array_equal(qs[k + 1], cand[pick].astype(np.float64))
+            if scales[pick] == 0.0:
+                pairs = []
+                d = -g[k + 1] * ik.step0 / np.abs(g[k + 1]).max()
+                restarts += 1
+                continue
+            s, y = qs[k + 1] - qs[k], g[k + 1] - g[k]
+            if s @ y > 0:
+                pairs.append((s, y))
+                trims += len(pairs) > ik.history
+                after_restart += k > 0 and out["pick"][k - 1, i] == 0
+                pairs = pairs[-ik.history:]
+                curv_steps += 1
+            d = _bfgs_direction(pairs, g[k + 1]) if pairs else -g[k + 1] * ik.step0 / np.abs(g[k + 1]).max()
+    assert restarts > 0 and curv_steps > 0 and trims > 0 and after_restart > 0  # every rule exercised

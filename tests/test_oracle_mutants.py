@@ -2,7 +2,7 @@
 
 Each case plants one mistake -- a dropped term, a wrong sign, a transposed
 operand, an index off by one, a wrong rounding rule -- in a temporary copy
-of the C oracle, builds that copy, and runs the pins of the part it touches
+of the C oracle (or of its Python front end), builds that copy, and runs the pins of the part it touches
 (the ``test_oracle_*`` modules, called with the mutant in place of the
 oracle).  At least one pin must fail.  A control case builds the unchanged
 source the same way and must pass every pin, so a harness error cannot pass
@@ -143,17 +143,39 @@ MUTANTS = [
 ]
 
 
-def _oracle_copy(tmp_path, replace=None):
+# The same for the oracle's Python part (the IK iteration loop of oracle.py).
+PY_MUTANTS = [
+    ("ik keeps the highest-cost candidate", ["ik"],
+     "pick = np.argmin(fc, axis=1)", "pick = np.argmax(fc, axis=1)"),
+    ("ik keeps the oldest pairs", ["ik"],
+     "hist[i] = hist[i][-ik.history:]", "hist[i] = hist[i][:ik.history]"),
+    ("ik restart keeps the history", ["ik"], "                hist[i] = []\n", "                pass\n"),
+    ("ik first step unscaled", ["ik"],
+     "return -g * (step0 / max(np.max(np.abs(g)), 1e-30))", "return -g"),
+    ("ik pairs kept without positive curvature", ["ik"], "if s @ y > 0.0:", "if True:"),
+    ("ik candidates not rounded to float32", ["ik"],
+     "cand = (q[:, None, :] + scales[None, :, None] * d[:, None, :]).astype(np.float32)",
+     "cand = q[:, None, :] + scales[None, :, None] * d[:, None, :]"),
+]
+
+
+def _oracle_copy(tmp_path, replace=None, py_replace=None):
     """The oracle's Python front end over a C library built from a copy of
-    vapr_oracle.c in tmp_path, with `replace` = (old, new) applied."""
+    vapr_oracle.c in tmp_path, with `replace` = (old, new) applied to the C
+    source and `py_replace` to the Python front end."""
     src = open(os.path.join(ORACLE_DIR, "vapr_oracle.c")).read()
     if replace:
         assert src.count(replace[0]) == 1, replace[0]
         src = src.replace(*replace)
     shutil.copy(os.path.join(ORACLE_DIR, "vapr_oracle.h"), tmp_path / "vapr_oracle.h")
     (tmp_path / "vapr_oracle.c").write_text(src)
+    py = open(os.path.join(ORACLE_DIR, "oracle.py")).read()
+    if py_replace:
+        assert py.count(py_replace[0]) == 1, py_replace[0]
+        py = py.replace(*py_replace)
+    (tmp_path / "oracle_copy.py").write_text(py)
     spec = importlib.util.spec_from_file_location(f"oracle_copy_{tmp_path.name}",
-                                                  os.path.join(ORACLE_DIR, "oracle.py"))
+                                                  str(tmp_path / "oracle_copy.py"))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     mod._HERE = str(tmp_path)
@@ -208,4 +230,10 @@ def test_unmutated_copy_passes_every_pin(tmp_path):
 @pytest.mark.parametrize("what,modules,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_pins_catch_planted_mistake(tmp_path, what, modules, old, new):
     orc = _oracle_copy(tmp_path, (old, new))
+    assert _first_failing_pin(orc, modules) is not None, f"no pin catches: {what}"
+
+
+@pytest.mark.parametrize("what,modules,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_catch_planted_mistake_in_python(tmp_path, what, modules, old, new):
+    orc = _oracle_copy(tmp_path, py_replace=(old, new))
     assert _first_failing_pin(orc, modules) is not None, f"no pin catches: {what}"
