@@ -52,3 +52,42 @@ def test_traffic_only_for_the_captured_source(monkeypatch):
     assert bench.kernel_traffic("collision", "fp32", 12345) is None
     monkeypatch.setattr(bench, "kernel_source_sha", lambda stage: "0" * 16)
     assert bench.kernel_traffic("collision", "fp32", 32768) is None
+
+
+def test_clock_summary():
+    """Clock samples as nvidia-smi prints them (csv, no header, no units):
+    median SM clock, the highest maximum, and every throttle reason seen."""
+    s = bench.ClockSampler(0)
+    s.out = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1995, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ])
+    out = s.summary()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    s.out = "0, 1200, 2070, 500.0, 0x8, Active, Not Active, Active, Not Active"
+    assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    s.out = ""
+    assert s.summary()["reasons"] == ["unsampled"]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the contract's keys; it needs no GPU."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0", "--workload", "single_128"],
+                       capture_output=True, text=True, timeout=300, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "configs/s" and line["value"] > 0
+    assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "single_128" and line["config"]["global_batch"] == 128
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "configs/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
