@@ -333,3 +333,19 @@ def test_noalloc_statuses():
     assert call(byref(_robot_struct()), byref(t), -1) == 1
     assert call(byref(_robot_struct()), byref(t), 0) == 0
     assert call(byref(_robot_struct()), byref(t), 1 << 20) == 6   # beyond the 64 MiB array
+
+
+def test_packed_row_bytes_agree_with_the_oracle():
+    """Row sizes of the packed layout, three ways: the library's
+    vapr_packed_row_bytes, the oracle's packer and the host format table,
+    for every format of the search set and the extra ones, at every row
+    length up to 300 and a few large ones."""
+    import oracle
+    fmts = F.search_set() + [F.fmt(5, 9), F.fmt(6, 8), F.fmt(6, 6)]
+    lengths = list(range(1, 301)) + [1023, 1 << 16, (1 << 20) + 3]
+    for f in fmts:
+        c = B.to_c_format(f)
+        for L in lengths:
+            want = oracle.packed_row_bytes(L, f.bits)
+            assert B.vapr_packed_row_bytes(L, c) == want == f.row_bytes(L), (str(f), L)
+    assert B.vapr_packed_row_bytes(0, B.to_c_format(F.FP32)) == 0
