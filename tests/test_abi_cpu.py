@@ -349,3 +349,24 @@ def test_packed_row_bytes_agree_with_the_oracle():
             want = oracle.packed_row_bytes(L, f.bits)
             assert B.vapr_packed_row_bytes(L, c) == want == f.row_bytes(L), (str(f), L)
     assert B.vapr_packed_row_bytes(0, B.to_c_format(F.FP32)) == 0
+
+
+def test_missing_library_fails_loudly():
+    """Without libvapr.so every call raises: there is no CPU or PyTorch
+    fallback (run in a child process so this one's loaded library stays)."""
+    import subprocess
+    import sys
+    code = (
+        "import paper_2310_07854_gb300.binding as B, paper_2310_07854_gb300.build as bld\n"
+        "from paper_2310_07854_gb300 import formats as F\n"
+        "bld.up_to_date = lambda: True\n"
+        "B.LIB_PATH = '/nonexistent/libvapr.so'\n"
+        "try:\n"
+        "    B.packed_row_bytes(156, F.FP32)\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+    )
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "raised: libvapr.so is missing" in r.stdout
