@@ -116,6 +116,19 @@ def test_bf16_and_fp8_match_torch(orc):
         assert np.array_equal(got, want), (E, M)
 
 
+def test_bf16_overflow_matches_torch(orc):
+    """At the top of the float32 range bfloat16 rounds to nearest even and
+    everything from the midpoint above its maximum up goes to Inf, as torch's
+    float32 -> bfloat16 cast does; Inf stays Inf."""
+    torch = pytest.importorskip("torch")
+    top = np.append(np.arange(0x7F7F0000, 0x7F800000, 7, dtype=np.uint32), np.uint32(0x7F800000))
+    x = np.concatenate([top, top | np.uint32(0x80000000)]).view(np.float32)
+    got = orc.encode(x, 8, 7)
+    want = torch.from_numpy(x.copy()).to(torch.bfloat16).view(torch.int16).numpy()
+    assert np.array_equal(got, want.astype(np.uint16).astype(np.uint32))
+    assert (got == 0x7F80).sum() > 100 and (got == 0x7F7F).sum() > 100
+
+
 def test_sub_byte_formats_match_ml_dtypes(orc):
     mld = pytest.importorskip("ml_dtypes")
     rng = np.random.default_rng(3)

@@ -143,7 +143,8 @@ MUTANTS = [
 ]
 
 
-# The same for the oracle's Python part (the IK iteration loop of oracle.py).
+# The same for the oracle's Python part (format classes, row sizes and the
+# IK iteration loop of oracle.py).
 PY_MUTANTS = [
     ("ik keeps the highest-cost candidate", ["ik"],
      "pick = np.argmin(fc, axis=1)", "pick = np.argmax(fc, axis=1)"),
@@ -153,6 +154,13 @@ PY_MUTANTS = [
     ("ik first step unscaled", ["ik"],
      "return -g * (step0 / max(np.max(np.abs(g)), 1e-30))", "return -g"),
     ("ik pairs kept without positive curvature", ["ik"], "if s @ y > 0.0:", "if True:"),
+    ("exmy E5M2 overflows to Inf", ["exmy"],
+     "    if (E, M) == (5, 2):\n        return IEEE | SAT", "    if (E, M) == (5, 2):\n        return IEEE"),
+    ("exmy E4M3 with Inf", ["exmy"], "        return FN | SAT", "        return IEEE | SAT"),
+    ("exmy bfloat16 saturates", ["exmy"],
+     "if (E, M) in ((8, 23), (8, 7), (5, 10)):", "if (E, M) in ((8, 23), (5, 10)):"),
+    ("pack rows padded to 8 bytes", ["exmy"],
+     "return -(-4 * words // 16) * 16", "return -(-4 * words // 8) * 8"),
     ("ik candidates not rounded to float32", ["ik"],
      "cand = (q[:, None, :] + scales[None, :, None] * d[:, None, :]).astype(np.float32)",
      "cand = q[:, None, :] + scales[None, :, None] * d[:, None, :]"),
