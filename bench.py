@@ -309,6 +309,12 @@ def sparsity(dist, grad, S: int) -> dict:
             "grad_spheres_nonzero": float((g != 0).any(-1).float().mean())}
 
 
+def speedup_pct(t_fp32: float, t_x: float) -> float:
+    """Speedup in the paper's form (Appendix, Detailed Experimental
+    Results): (T_FP32 / T_x - 1) x 100 %; negative when x is slower."""
+    return (t_fp32 / t_x - 1.0) * 100.0
+
+
 def fp32_peak_tflops(peaks) -> float:
     """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x max SM clock."""
     return 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
@@ -880,7 +886,8 @@ def main():
             "config": workload_config(w, world),
             "roofline": roof,
             "vapr": {"table": str(vtable), "value": value_v, "unit": "configs/s",
-                     "speedup_vs_fp32": value_v / value, "ms_per_step": tv / args.steps,
+                     "speedup_vs_fp32": value_v / value, "speedup_pct": speedup_pct(t32, tv),
+                     "ms_per_step": tv / args.steps,
                      "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale},
             "stages": stages,
             "sparsity": sparse,

@@ -91,3 +91,9 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "configs/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_speedup_in_the_papers_form():
+    assert bench.speedup_pct(1.0, 0.5) == 100.0
+    assert abs(bench.speedup_pct(1.0, 1 / 1.0628) - 6.28) < 1e-9
+    assert bench.speedup_pct(0.96, 1.0) < 0  # slower: negative
