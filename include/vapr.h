@@ -212,11 +212,16 @@ vapr_status vapr_fk(const vapr_robot* robot, const float* q, int64_t n,
  * gradient at exactly zero penetration is 0, and a self pair at zero
  * distance adds no gradient.  Each configuration's outputs depend on that
  * configuration alone (fixed summation orders), whatever the batch, the
- * scene grid or the order in which the kernel's warps take configurations;
- * launches on different streams, and replays of captured launches, may
- * overlap.  The call keeps a small host-side record per device for the
- * kernel's work counters (an event per recent launch); it allocates no
- * device memory. */
+ * scene grid or the order in which the kernel's warps take configurations.
+ * Launches made outside stream capture may overlap one another (on other
+ * streams or host threads), and so may successive replays of one
+ * instantiated graph, which CUDA runs one after another.  A launch captured
+ * into a graph owns one work counter for good: every executable instance
+ * of that capture (a second cudaGraphInstantiate, a cudaGraphClone, the
+ * graph embedded twice as a child node) shares it, so two such instances
+ * must not run at the same time.  The call keeps a small host-side record
+ * per device for the kernel's work counters (an event per recent launch);
+ * it allocates no device memory. */
 vapr_status vapr_collision_cost(const vapr_robot* robot, const vapr_scene* scene,
                                 const vapr_cost_params* params,
                                 const void* pos_packed, int64_t n,
@@ -441,7 +446,10 @@ vapr_status vapr_batched_eval(const vapr_batch_plan* plan, int32_t* dev_status, 
  *  - Nothing is allocated: no cudaMalloc, cudaFree or allocating library
  *    call.  The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current and caches it; make
- *    that first call before any stream capture.
+ *    that first call before any stream capture.  The cached address is not
+ *    looked up again, so it does not survive cudaDeviceReset (which
+ *    recreates the device's context): a process that resets a device must
+ *    not call this entry point on that device afterwards.
  *  - Returns VAPR_ERR_TOO_LARGE when vapr_cost_grad_workspace_bytes(robot,
  *    n, table) exceeds VAPR_NOALLOC_SCRATCH_BYTES (FP32 storage with 52
  *    spheres: up to 53,773 configurations per call).

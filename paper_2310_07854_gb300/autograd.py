@@ -59,13 +59,25 @@ class VaprCost(torch.nn.Module):
     collision cost C [n] of joint configurations q [n, J], differentiable in q.
 
     ``recompute_fk=True`` recomputes the joint chain in backward instead of
-    storing the link transforms (12 values per joint and configuration)."""
+    storing the link transforms (12 values per joint and configuration).
+
+    A scene given as host arrays gets the collision stage's broad-phase
+    grid, as ``path.Evaluator`` builds it (``grid_cells``: "auto" for the
+    finest up to 128 cells per axis that fits 32 MiB, a cell count, or None
+    for no grid); a DeviceScene is used as it is.  The grid changes which
+    cuboids the kernel visits, never a result bit."""
 
     def __init__(self, robot, scene, params, table: F.FormatTable = F.FP32_TABLE,
-                 recompute_fk: bool = True, keep_dist: bool = False, device="cuda"):
+                 recompute_fk: bool = True, keep_dist: bool = False, device="cuda",
+                 grid_cells="auto"):
         super().__init__()
+        from .path import attach_grid
         self.robot = robot if isinstance(robot, B.DeviceRobot) else B.DeviceRobot(robot, device)
-        self.scene = scene if isinstance(scene, B.DeviceScene) else B.DeviceScene(scene, device)
+        if isinstance(scene, B.DeviceScene):
+            self.scene = scene
+        else:
+            self.scene = B.DeviceScene(scene, device)
+            attach_grid(self.scene, self.robot, params, grid_cells)
         self.cparams = B.cost_params(params)
         self.table = table
         self.ctable = B.to_c_table(table)

@@ -20,13 +20,24 @@ def auto_grid_cells(n_cuboids: int, budget: int = 32 << 20) -> int:
     return cells
 
 
+def attach_grid(scene, robot, params, grid_cells="auto") -> None:
+    """Builds the broad-phase grid of a DeviceScene for the robot's largest
+    sphere radius and the margin eta: grid_cells cells per axis ("auto":
+    auto_grid_cells; None or 0: no grid)."""
+    import numpy as np
+    if grid_cells == "auto":
+        grid_cells = auto_grid_cells(scene.c.n_cuboids)
+    if grid_cells:
+        reach = float(np.max(robot.host.sphere_local[:, 3]))
+        scene.build_grid(reach, params.eta, grid_cells)
+
+
 class Evaluator:
     def __init__(self, robot, scene, params, n_max: int, table: F.FormatTable = F.FP32_TABLE,
                  recompute_fk: bool = True, device: str = "cuda", grid_cells: int | str | None = "auto"):
         """A scene given as host arrays gets a broad-phase grid of grid_cells
         cells per axis ("auto": the finest up to 128 whose grid fits 32 MiB;
         None: no grid); a DeviceScene is used as it is."""
-        import numpy as np
         import torch
         self.torch = torch
         self.robot = robot if isinstance(robot, B.DeviceRobot) else B.DeviceRobot(robot, device)
@@ -34,11 +45,7 @@ class Evaluator:
             self.scene = scene
         else:
             self.scene = B.DeviceScene(scene, device)
-            if grid_cells == "auto":
-                grid_cells = auto_grid_cells(self.scene.c.n_cuboids)
-            if grid_cells:
-                reach = float(np.max(self.robot.host.sphere_local[:, 3]))
-                self.scene.build_grid(reach, params.eta, grid_cells)
+            attach_grid(self.scene, self.robot, params, grid_cells)
         self.params = B.cost_params(params)
         self.table = table
         self.ctable = B.to_c_table(table)  # built once: calls pass the C struct

@@ -91,3 +91,22 @@ def test_two_pending_forwards():
     assert torch.equal(ga, qa2.grad)
     cb.sum().backward()
     assert torch.isfinite(qb.grad).all()
+
+
+def test_autograd_uses_the_scene_grid():
+    """VaprCost builds the broad-phase grid for a host scene, and its cost and
+    gradient equal the grid-less module's bit for bit (the grid only narrows
+    which cuboids the kernel visits)."""
+    import torch
+    from paper_2310_07854_gb300.autograd import VaprCost
+    w = synth.make_workload("particle_32768")
+    with_grid = VaprCost(w.robot, w.scene, w.params)
+    plain = VaprCost(w.robot, w.scene, w.params, grid_cells=None)
+    assert with_grid.scene.grid is not None and plain.scene.grid is None
+    out = []
+    for mod in (with_grid, plain):
+        q = to_dev(w.q).requires_grad_(True)
+        c = mod(q)
+        c.sum().backward()
+        out.append((c.detach(), q.grad))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
