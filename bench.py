@@ -35,7 +35,8 @@ from paper_2310_07854_gb300 import replicas  # noqa: E402
 from paper_2310_07854_gb300 import synth  # noqa: E402
 
 WORKLOAD = "particle_32768"
-VAPR_TABLE = "P=E5M10,D=E2M1,G=E2M1,J=E4M3"
+# example reduced table for the single-stage profiling mode (--kernel)
+EXAMPLE_TABLE = "P=E5M10,D=E2M1,G=E2M1,J=E4M3"
 METRIC = "configs/s for FK+collision cost+grad, % of HBM roofline; VaPr vs FP32 at stated err"
 
 
@@ -46,16 +47,19 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="vapr", choices=["vapr", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=list(synth.WORKLOADS))
-    ap.add_argument("--table", default=VAPR_TABLE, help="format table of the VaPr leg")
+    ap.add_argument("--table", default="searched",
+                    help="format table of the VaPr leg: 'searched' (the table the VaPr search finds within "
+                         "its error budget) or a table string; with --kernel, 'searched' means " + EXAMPLE_TABLE)
     ap.add_argument("--grid-cells", type=int, default=-1,
                     help="cells per axis of the scene's broad-phase grid (0: none, -1: the evaluator's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-dram-scale", action="store_true")
+    ap.add_argument("--no-dram-scale", action="store_true", help="skip the DRAM-scale sweep")
+    ap.add_argument("--no-config-baselines", action="store_true",
+                    help="skip timing configs 1-3 beside the oracle (1 thread and all threads)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the learned-surrogate leg (training + gated collision)")
     ap.add_argument("--surrogate-epochs", type=int, default=80)
-    ap.add_argument("--no-search", action="store_true", help="skip the VaPr format search leg")
     ap.add_argument("--kernel", choices=["fk", "collision", "backward", "mlp_infer", "step", "ceiling"],
                     default=None,
                     help="profiling mode: run only this stage (--warmup launches, then --steps timed) on "
@@ -380,13 +384,13 @@ def ceiling_leg(w, ev32, q, n, flush, torch, peak_alu, reps=16, rounds=5):
                         "distances that pass, no scene grid, no packed rows"}}
 
 
-def search_leg(w, ev32, q, n, args, flush, torch, per32):
+def search_tables(w, ev32, args):
     """VaPr search (Sec. V-A) for the workload: per-tensor binary search and
     the combinatorial search on a 1024-configuration validation batch with a
-    5 % budget on C and J against the FP32 path, then the found table timed
-    on the full workload next to FP32."""
+    5 % budget on C and J against the FP32 path; then the same search over
+    the formats with a one-instruction converter.  Returns (table, report,
+    hardware-only table)."""
     from paper_2310_07854_gb300 import search as S
-    from paper_2310_07854_gb300.path import Evaluator
     tensors = ("pos", "dist", "grad", "jgrad")
     t0 = time.perf_counter()
     ev = S.CachedEvaluator(S.PathEvaluator(ev32.robot, ev32.scene, w.params, synth.make_q(901, 1024)))
@@ -394,31 +398,106 @@ def search_leg(w, ev32, q, n, args, flush, torch, per32):
     space = S.reduced_space(per)
     start = F.FormatTable(**{k: space[k][0] for k in tensors})
     best, e, _ = S.combinatorial_search(ev, space, samples=args.search_samples, seed=0, seeds=[start])
-    search_s = time.perf_counter() - t0
-    out = {"budget": "max|C-C32| <= 5% max|C32| and max|J-J32| <= 5% max|J32| (1024 validation configs)",
-           "per_tensor_min_bits": {k: v[0] for k, v in per.items()}, "reduced_space": S.space_size(space),
-           "evaluations": ev.count, "search_s": search_s}
-
-    def timed(best, e):
-        evb = Evaluator(ev32.robot, ev32.scene, w.params, n, best)
-        pb = time_steps(evb, q, n, args.steps, args.warmup, flush, torch)
-        return {"table": str(best), "bits_searched_tensors": sum(getattr(best, k).bits for k in tensors),
-                "validation_error": e.error,
-                "configs_per_s": n * args.steps / (sum(pb["step"]) / 1000.0),
-                "speedup_vs_fp32": sum(per32["step"]) / sum(pb["step"]),
-                "stage_ms": {k: statistics.mean(pb[k]) for k in ("fk", "collision", "backward") if pb[k]}}
-
-    if best is not None:
-        out.update(timed(best, e))
-    # the same search restricted to formats with a one-instruction converter
     hw = F.hardware_formats()
     per_hw = S.per_tensor_search(ev, tensors, candidates=hw)
     space_hw = S.reduced_space(per_hw, hw)
     start_hw = F.FormatTable(**{k: space_hw[k][0] for k in tensors})
     best_hw, e_hw, _ = S.combinatorial_search(ev, space_hw, samples=args.search_samples, seed=0, seeds=[start_hw])
-    if best_hw is not None:
-        out["hardware_formats_only"] = {"reduced_space": S.space_size(space_hw), **timed(best_hw, e_hw)}
+    report = {"budget": "max|C-C32| <= 5% max|C32| and max|J-J32| <= 5% max|J32| (1024 validation configs)",
+              "per_tensor_min_bits": {k: v[0] for k, v in per.items()}, "reduced_space": S.space_size(space),
+              "evaluations": ev.count, "search_s": time.perf_counter() - t0,
+              "table": str(best) if best is not None else None,
+              "bits_searched_tensors": sum(getattr(best, k).bits for k in tensors) if best is not None else None,
+              "validation_error": e.error if best is not None else None,
+              "hardware_formats_only": {"reduced_space": S.space_size(space_hw),
+                                        "table": str(best_hw) if best_hw is not None else None,
+                                        "validation_error": e_hw.error if best_hw is not None else None}}
+    return best, report, best_hw
+
+
+def dram_sweep(w, robot_dev, tables, flush, torch, peaks, exps=range(15, 21), counts=(8, 40)):
+    """Per-stage time and HBM fraction from 2^15 to 2^20 configurations, with
+    the 8-cuboid scene of the single-problem workload and the 40-cuboid
+    scene of the benchmark, for each format table; L2 flushed before every
+    step (median of 3 steps after 2 untimed)."""
+    from paper_2310_07854_gb300.path import Evaluator
+    nmax = 1 << max(exps)
+    qmax = torch.as_tensor(synth.make_q(77, nmax), device="cuda")
+    scenes = {w.scene.n_cuboids: w.scene, 8: synth.make_workload("single_128").scene}
+    out = []
+    for O in counts:
+        scene = scenes.get(O) or synth.make_scene(1 + O, O)
+        for tname, table in tables.items():
+            ev = Evaluator(robot_dev, scene, w.params, nmax, table)
+            bp = ev.bytes_per_config()
+            for e in exps:
+                n = 1 << e
+                per = time_steps(ev, qmax, n, 3, 2, flush, torch)
+                row = {"cuboids": O, "table": tname, "n_configs": n,
+                       "configs_per_s": n / (statistics.median(per["step"]) / 1000.0)}
+                for k in ("fk", "collision", "backward"):
+                    ms = statistics.median(per[k])
+                    row[k] = {"ms": ms, "hbm_frac": bp[k] * n / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]}
+                out.append(row)
+            del ev
+    del qmax
     return out
+
+
+def config_baselines(args, flush, torch):
+    """Configs 1-3 (single_128, sweep_1024, particle_32768): the FP32 step on
+    the GPU (median of >= 20 steps, L2 flushed before each) beside the FP64
+    oracle as it stands on one host thread and on all host threads (median
+    of 5 runs each)."""
+    import oracle
+    from paper_2310_07854_gb300.path import Evaluator
+    oracle.build()
+    threads = oracle.num_threads()
+    out = {}
+    try:
+        for name in ("single_128", "sweep_1024", "particle_32768"):
+            w = synth.make_workload(name)
+            q = torch.as_tensor(w.q, device="cuda")
+            ev = Evaluator(w.robot, w.scene, w.params, w.n, F.FP32_TABLE)
+            per = time_steps(ev, q, w.n, max(args.steps, 20), max(args.warmup, 3), flush, torch)
+            ms = statistics.median(per["step"])
+            res = {"configs": w.n, "cuboids": w.scene.n_cuboids,
+                   "gpu_fp32": {"ms_median": ms, "configs_per_s": w.n / (ms / 1000.0)}}
+            for label, th in (("oracle_1_thread", 1), ("oracle_all_threads", threads)):
+                oracle.set_num_threads(th)
+                ts = []
+                for _ in range(5):
+                    t0 = time.perf_counter()
+                    oracle.cost_and_grad(w.robot, w.scene, w.params, w.q)
+                    ts.append(time.perf_counter() - t0)
+                res[label] = {"threads": th, "s_median_of_5": statistics.median(ts),
+                              "configs_per_s": w.n / statistics.median(ts)}
+            res["gpu_over_oracle_all_threads"] = (res["gpu_fp32"]["configs_per_s"]
+                                                  / res["oracle_all_threads"]["configs_per_s"])
+            out[name] = res
+            del ev
+    finally:
+        oracle.set_num_threads(threads)
+    out["host"] = {"threads": threads, "cpu": host_cpu_name()}
+    return out
+
+
+def host_cpu_name() -> str:
+    """The host CPU's model name as /proc/cpuinfo gives it (x86: model name;
+    Arm: implementer and part), else the machine type."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    parts = {l.split(":")[0].strip(): l.split(":", 1)[1].strip() for l in info if ":" in l}
+    if "CPU part" in parts:
+        return f"{platform.machine()} implementer {parts.get('CPU implementer')} part {parts['CPU part']}"
+    return platform.machine()
 
 
 def swept_leg(w, ev32, n, args, flush, torch, samples=4):
@@ -521,18 +600,38 @@ def ik_leg(w, ev32, args, torch, n_seeds=4096, iters=50):
             "pose_only": ik_pose_only(w, ev32, torch, n_seeds)}
 
 
-def fused_leg(w, q, n, vtable, args, flush, torch):
-    """FK, collision and backward fused per tile in one persistent launch
-    (the multi-problem kernel on this single problem): P and G never leave
-    the per-block scratch slices, which stay in L2."""
+def fused_leg(w, ev32, q, n, vtable, args, flush, torch, sizes=(None, 1 << 20)):
+    """The step in one kernel with P and G kept on the SM (vapr_cost_grad_fused:
+    the upper bound of not storing them at all) timed beside the staged
+    step (vapr_cost_grad: FK, collision, backward with P and G stored in
+    their formats), FP32 and the VaPr table, at the workload's size and at
+    2^20 configurations; and the multi-problem persistent kernel run on this
+    single problem (P and G in per-block scratch)."""
+    from paper_2310_07854_gb300 import binding as B
     from paper_2310_07854_gb300.batched import BatchedEvaluator
-    out = {}
-    for name, table in (("fp32", F.FP32_TABLE), ("vapr", vtable)):
-        be = BatchedEvaluator([w], table=table, tile=128)
-        ms = time_graph(be.eval, args.steps, args.warmup, flush, torch)
-        out[name] = {"configs_per_s": n / (ms / 1000.0), "ms": ms, "tile": 128,
-                     "status": be.device_status()}
-        del be
+    S, J = w.robot.n_spheres, w.robot.n_joints
+    out = {"sizes": []}
+    for size in sizes:
+        nn = n if size is None else size
+        qq = q if size is None else torch.as_tensor(synth.make_q(77, nn), device="cuda")
+        row = {"n_configs": nn}
+        for name, table in (("fp32", F.FP32_TABLE), ("vapr", vtable)):
+            cost = torch.empty(nn, device="cuda")
+            jg = B.alloc_packed(nn, J, table.jgrad)
+            ws = B.alloc_workspace(ev32.robot, nn, table)
+            staged = time_graph(lambda: B.vapr_cost_grad(ev32.robot, ev32.scene, w.params, qq, nn, table, None,
+                                                         cost, None, jg, ws), args.steps, args.warmup, flush, torch)
+            fused = time_graph(lambda: B.vapr_cost_grad_fused(ev32.robot, ev32.scene, w.params, qq, nn, table, None,
+                                                              cost, None, jg), args.steps, args.warmup, flush, torch)
+            row[name] = {"table": str(table), "staged_ms": staged, "fused_ms": fused,
+                         "fused_configs_per_s": nn / (fused / 1000.0), "fused_over_staged": staged / fused}
+            del ws, jg, cost
+        out["sizes"].append(row)
+    be = BatchedEvaluator([w], table=F.FP32_TABLE, tile=128)
+    ms = time_graph(be.eval, args.steps, args.warmup, flush, torch)
+    out["multi_problem_kernel_on_one_problem"] = {"configs_per_s": n / (ms / 1000.0), "ms": ms, "tile": 128,
+                                                  "status": be.device_status()}
+    del be
     return out
 
 
@@ -660,7 +759,8 @@ def kernel_mode(args):
     w = synth.make_workload(args.workload)
     n = args.configs or w.n
     q = torch.as_tensor(synth.make_q(500, n), device="cuda")
-    table = F.FormatTable.parse(args.table) if args.table != "fp32" else F.FP32_TABLE
+    spec = EXAMPLE_TABLE if args.table == "searched" else args.table
+    table = F.FormatTable.parse(spec) if spec != "fp32" else F.FP32_TABLE
     if args.kernel == "ceiling":
         ev = Evaluator(w.robot, w.scene, w.params, n, F.FP32_TABLE)
         l2 = torch.cuda.get_device_properties(0).L2_cache_size
@@ -726,9 +826,15 @@ def main():
     q = torch.as_tensor(w.q, device="cuda")
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
     flush = torch.zeros(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
-    vtable = F.FormatTable.parse(args.table)
     ev32 = Evaluator(w.robot, w.scene, w.params, n, F.FP32_TABLE,
                      grid_cells="auto" if args.grid_cells < 0 else (args.grid_cells or None))
+    found, vtable_hw = None, None
+    if args.table == "searched":  # the VaPr leg times the table the search finds within its budget
+        vtable, found, vtable_hw = search_tables(w, ev32, args)
+        if vtable is None:
+            raise SystemExit("the VaPr search found no table within its budget")
+    else:
+        vtable = F.FormatTable.parse(args.table)
     evv = Evaluator(ev32.robot, ev32.scene, w.params, n, vtable)
 
     def barrier():
@@ -841,32 +947,28 @@ def main():
            "eager_step_host": {"value": world * n * args.steps / te_eager, "unit": "configs/s",
                                "launches_per_step": 4, "copies_per_step": 3}}
 
-    dram = None
+    sweep = None
     if not args.no_dram_scale:
-        nb = 1 << 20
-        qb = torch.as_tensor(synth.make_q(77, nb), device="cuda")
-        ebig = Evaluator(ev32.robot, ev32.scene, w.params, nb, F.FP32_TABLE)
-        pb = time_steps(ebig, qb, nb, 3, 2, flush, torch)
-        ebv = Evaluator(ev32.robot, ev32.scene, w.params, nb, vtable)
-        pbv = time_steps(ebv, qb, nb, 3, 2, flush, torch)
-        dram = {"n_configs": nb}
-        for ev_, per_, name in ((ebig, pb, "fp32"), (ebv, pbv, "vapr")):
-            bp = ev_.bytes_per_config()
-            dram[name] = {"configs_per_s": nb * 3 / (sum(per_["step"]) / 1000.0)}
-            for k in ("fk", "collision", "backward"):
-                ms = statistics.mean(per_[k])
-                dram[name][k] = {"ms": ms, "hbm_frac": bp[k] * nb / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]}
-        del ebig, ebv, qb
+        sweep = dram_sweep(w, ev32.robot, {"fp32": F.FP32_TABLE, "vapr": vtable}, flush, torch, peaks)
+    bases = None
+    if rank == 0 and world == 1 and not args.no_config_baselines:
+        bases = config_baselines(args, flush, torch)
 
     broad = broad_phase_leg(w, ev32, q, n, args, flush, torch)
-    fused = fused_leg(w, q, n, vtable, args, flush, torch)
+    fused = fused_leg(w, ev32, q, n, vtable, args, flush, torch)
     ev32.fk(q, n)
     swept = swept_leg(w, ev32, n, args, flush, torch)
     ik_res = ik_leg(w, ev32, args, torch)
 
-    found = None
-    if not args.no_search:
-        found = search_leg(w, ev32, q, n, args, flush, torch, per32)
+    if found is not None:  # the hardware-converter table, timed beside
+        hw = found["hardware_formats_only"]
+        if vtable_hw is not None:
+            evh = Evaluator(ev32.robot, ev32.scene, w.params, n, vtable_hw)
+            ph = time_steps(evh, q, n, args.steps, args.warmup, flush, torch)
+            hw.update({"configs_per_s": n * args.steps / (sum(ph["step"]) / 1000.0),
+                       "speedup_vs_fp32": sum(per32["step"]) / sum(ph["step"]),
+                       "stage_ms": {k: statistics.mean(ph[k]) for k in ("fk", "collision", "backward") if ph[k]}})
+            del evh
 
     sur = None
     if not args.no_surrogate:
@@ -885,15 +987,18 @@ def main():
             "data": "synthetic",
             "config": workload_config(w, world),
             "roofline": roof,
-            "vapr": {"table": str(vtable), "value": value_v, "unit": "configs/s",
+            "vapr": {"table": str(vtable), "source": "VaPr search within its budget" if found else "--table",
+                     "value": value_v, "unit": "configs/s",
                      "speedup_vs_fp32": value_v / value, "speedup_pct": speedup_pct(t32, tv),
                      "ms_per_step": tv / args.steps,
-                     "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale},
+                     "max_abs_err_vs_fp32_path": err, "fp32_max_abs": err_scale,
+                     "max_err_rel_to_fp32_max": {k: err[k] / err_scale[k] if err_scale[k] else None for k in err},
+                     "stage_ms": {k: statistics.mean(perv[k]) for k in ("fk", "collision", "backward") if perv[k]}},
             "stages": stages,
             "sparsity": sparse,
             "alu_ceiling": ceil,
             "broad_phase": broad,
-            "fused_single_launch": fused,
+            "fused": fused,
             "swept": swept,
             "ik": ik_res,
             "vapr_search": found,
@@ -901,7 +1006,8 @@ def main():
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
             "cpu_baseline": cb,
-            "dram_scale": dram,
+            "dram_sweep": sweep,
+            "config_baselines": bases,
             "surrogate": sur,
         }
         print(json.dumps(line), flush=True)

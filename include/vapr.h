@@ -374,6 +374,20 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
                            void* dist_packed, void* jgrad_packed, void* workspace,
                            size_t workspace_bytes, void* stream);
 
+/* The same step as vapr_cost_grad in one kernel, with the sphere centres P
+ * and their gradient G kept on the SM, never written to device memory: the
+ * fused upper bound of the staged design (not storing the large tensors at
+ * all, against storing them in reduced formats, Sec. III-C).  P and G are
+ * still rounded to table->pos and table->grad in registers, as storing and
+ * loading them would.  Same arguments as vapr_cost_grad without the
+ * workspace.  cost and the D rows equal vapr_cost_grad's bit for bit; the
+ * joint gradient sums the same terms in another order (per link, then over
+ * links) and agrees with it to float32 rounding. */
+vapr_status vapr_cost_grad_fused(const vapr_robot* robot, const vapr_scene* scene,
+                                 const vapr_cost_params* params, const float* q, int64_t n,
+                                 const vapr_format_table* table, const float* dcost, float* cost,
+                                 void* dist_packed, void* jgrad_packed, void* stream);
+
 /* ---- many uneven problems in one persistent launch ------------------------ */
 /* One planning problem of an uneven batch (device pointers, as for
  * vapr_cost_grad): its own arm tables, obstacles, parameters,

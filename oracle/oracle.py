@@ -79,6 +79,7 @@ def _load():
                                    dbl, P, P, P, P, i64, P, P]),
             "or_lbfgs_direction": (None, [i32, i32, P, P, P, P]),
             "or_num_threads": (i32, []),
+            "or_set_num_threads": (None, [i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -98,6 +99,11 @@ def _p(a):
 
 def num_threads() -> int:
     return int(_load().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops over configurations from now on."""
+    _load().or_set_num_threads(int(n))
 
 
 # ----------------------------------------------------------------- formats

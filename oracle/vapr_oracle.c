@@ -20,6 +20,16 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Threads of the later parallel loops (n >= 1); the arithmetic of each
+ * configuration does not depend on it. */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ========================================================================= */
 /* ExMy emulator.  Sec. IV-A: a format has 1 sign bit, E exponent bits and M
  * mantissa bits.  Reading: IEEE-style bias 2^(E-1)-1 with subnormals; the

@@ -153,6 +153,8 @@ double or_mlp_grads(const float* params, int H, const float* x, const float* y, 
                     double over_weight, double* grads);
 
 int or_num_threads(void);
+/* threads of the parallel loops over configurations from now on (n >= 1) */
+void or_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -128,6 +128,9 @@ SIGNATURES = {
                                       ctypes.POINTER(vapr_cost_params), _P, _i64,
                                       ctypes.POINTER(vapr_format_table), _P, _P, _P, _P, _P,
                                       ctypes.c_size_t, _P]),
+    "vapr_cost_grad_fused": (ctypes.c_int, [ctypes.POINTER(vapr_robot), ctypes.POINTER(vapr_scene),
+                                            ctypes.POINTER(vapr_cost_params), _P, _i64,
+                                            ctypes.POINTER(vapr_format_table), _P, _P, _P, _P, _P]),
     "vapr_batched_plan_bytes": (ctypes.c_size_t, [ctypes.POINTER(vapr_problem), ctypes.c_int32,
                                                   ctypes.POINTER(vapr_format_table),
                                                   ctypes.POINTER(vapr_batch_tuning)]),
@@ -419,6 +422,17 @@ def vapr_cost_grad(robot: DeviceRobot, scene: DeviceScene, params, q, n, table, 
                                   _ptr(q), n, ctypes.byref(ct), _ptr(dcost), _ptr(cost),
                                   _ptr(dist_packed), _ptr(jgrad_packed), _ptr(workspace),
                                   nbytes, _stream(stream)), "vapr_cost_grad")
+
+
+def vapr_cost_grad_fused(robot: DeviceRobot, scene: DeviceScene, params, q, n, table, dcost, cost,
+                         dist_packed, jgrad_packed, stream=None):
+    """The step in one kernel, P and G kept on the SM (see include/vapr.h)."""
+    ct = to_c_table(table)
+    cp = params if isinstance(params, vapr_cost_params) else cost_params(params)
+    _check(_load().vapr_cost_grad_fused(ctypes.byref(robot.c), ctypes.byref(scene.c), ctypes.byref(cp),
+                                        _ptr(q), n, ctypes.byref(ct), _ptr(dcost), _ptr(cost),
+                                        _ptr(dist_packed), _ptr(jgrad_packed), _stream(stream)),
+           "vapr_cost_grad_fused")
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20  # VAPR_NOALLOC_SCRATCH_BYTES

@@ -1,6 +1,7 @@
 // C ABI entry points (include/vapr.h): argument checks, format tables and
 // the pack/unpack converter kernels.  Every check happens before anything is
 // enqueued; kernels themselves never abort.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -64,6 +65,8 @@ DevFmt make_dev_fmt(vapr_format fm) {
   f.nan_code = (f.ieee || f.fn) ? ((f.all_e << f.M) | f.all_m) : f.max_code;
   f.ovf_inf = f.ieee && !sat;
   const unsigned fl = fm.flags;
+  f.fastdec = f.E < 8 && !f.ieee && !f.fn;
+  f.dec_scale = std::ldexp(1.0f, 127 - f.bias);
   f.kind = KIND_GENERIC;
   if (f.E == 5 && f.M == 10 && fl == VAPR_FMT_IEEE) f.kind = KIND_F16;
   if (f.E == 8 && f.M == 7 && fl == VAPR_FMT_IEEE) f.kind = KIND_BF16;
@@ -424,6 +427,28 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
   if (e == cudaSuccess)
     e = launch_backward(r, q, none, grad, dcost, n, packed(jgrad_packed, r.J, table->jgrad), s);
   return cuda_status(e);
+}
+
+vapr_status vapr_cost_grad_fused(const vapr_robot* robot, const vapr_scene* scene,
+                                 const vapr_cost_params* params, const float* q, int64_t n,
+                                 const vapr_format_table* table, const float* dcost, float* cost,
+                                 void* dist_packed, void* jgrad_packed, void* stream) {
+  RobotArgs r;
+  vapr_status st = check_robot(robot, &r);
+  if (st != VAPR_OK) return st;
+  if ((st = check_table(table)) != VAPR_OK) return st;
+  if (!params) return VAPR_ERR_INVALID_ARG;
+  SceneArgs sc;
+  if ((st = check_scene(scene, &sc)) != VAPR_OK) return st;
+  if (n < 0) return VAPR_ERR_INVALID_ARG;
+  if (n > VAPR_MAX_CONFIGS) return VAPR_ERR_TOO_LARGE;
+  if (n == 0) return VAPR_OK;
+  if (!q || !cost || !jgrad_packed) return VAPR_ERR_INVALID_ARG;
+  if (!aligned(q, 4) || !aligned(cost, 4) || (dcost && !aligned(dcost, 4)) || !aligned(jgrad_packed, 16) ||
+      (dist_packed && !aligned(dist_packed, 16)))
+    return VAPR_ERR_MISALIGNED;
+  return cuda_status(launch_fused(r, sc, *params, q, dcost, n, *table, cost, packed(dist_packed, r.S, table->dist),
+                                  packed(jgrad_packed, r.J, table->jgrad), (cudaStream_t)stream));
 }
 
 vapr_status vapr_backward(const vapr_robot* robot, const float* q, const void* xform_packed,

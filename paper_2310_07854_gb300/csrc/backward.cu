@@ -13,63 +13,43 @@
 // and the totals finish every J_j at the end.  Zero gradients are skipped
 // (the sparsity of Sec. III-C).
 //
-// One thread per configuration; a warp owns 32 consecutive configurations.
-// Their gradient rows are contiguous in global memory, so lane 0 stages
-// them into shared memory with a single TMA bulk copy (cp.async.bulk,
-// completion counted in bytes on an mbarrier) while the lanes start on the
-// joint chain; each lane then reads its own row with 16-byte shared loads.
-// Every wait on the mbarrier is bounded: on timeout the kernel records
-// VAPR_ERR_TIMEOUT in a device word (vapr_device_error), drains its own copy
-// (again bounded) and stops.  When a block's staging buffers would not fit
-// in shared memory, lanes stream their rows from global memory instead.
+// One thread per configuration; a warp owns tiles of 32 consecutive
+// configurations, whose gradient rows are contiguous in global memory.  The
+// kernel is bound by streaming those rows (624 bytes per configuration in
+// float32), so each warp streams them through a small ring of shared-memory
+// slots (SegReader): a slot holds one segment of the tile, SEG_W = 12 words
+// of each of the 32 rows, copied in by the lanes with 16-byte cp.async
+// copies laid out so that each copy instruction reads whole runs of about
+// 11 consecutive rows.  The threads read their rows' values in increasing
+// order; when a segment is done the warp hands its slot to the copy
+// SEG_SLOTS segments ahead, so copies stay in flight while the warp
+// computes.  A segment row of 12 words holds whole spheres (4k of them at k
+// values per word), so each sphere costs one segment check and three 32-bit
+// shared loads.  A slot is small (1.5 KB), so many warps fit per SM.  (A
+// 2-D TMA copy per segment was measured first: the TMA unit took about 210
+// cycles per 32-row box of 48-byte rows, which held the kernel to
+// 2.3 TB/s.)  The q rows of the next tile are copied the same way while
+// the warp works on the current one.  The joint loop stays a loop (the
+// per-joint terms go to shared memory): unrolling it over 7 joints made the
+// code too large for the instruction cache.
+//
+// Reading values in increasing order needs the robot's spheres grouped by
+// link in increasing link order (the order the pass walks them in); the
+// block checks this, and otherwise the threads read their rows straight
+// from global memory.  The kernel has no waits other than on its own
+// asynchronous copies.
 #include "stages.cuh"
 
 namespace vapr {
 
 constexpr int BW_WARPS = 4;
 constexpr int BW_BLOCK = 32 * BW_WARPS;
-constexpr unsigned long long BW_WAIT_LIMIT = 1ull << 24;  // ~1 s of 64 ns sleeps
+constexpr int SEG_W = 12;     // words of each row per segment (48 B)
+constexpr int SEG_SLOTS = 3;  // ring slots per warp
+constexpr uint32_t SEG_BYTES = 32u * SEG_W * 4u;
+static_assert(SEG_W == 12, "a segment row holds 12k values = 4k whole spheres");
 
-__device__ int g_backward_error;  // sticky: first error code, 0 if none
-
-// ---- mbarrier / bulk-copy wrappers (PTX ISA: mbarrier, cp.async.bulk)
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase) {
-  uint32_t done;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(phase)
-      : "memory");
-  return done != 0;
-}
-// Bounded wait for the phase to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  for (unsigned long long it = 0; it < BW_WAIT_LIMIT; ++it) {
-    if (mbar_test(bar, phase)) return true;
-    __nanosleep(64);
-  }
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
+__device__ int g_backward_error;  // sticky: first error code, 0 if none (no wait here can time out)
 
 struct BwArgs {
   RobotArgs r;
@@ -77,73 +57,190 @@ struct BwArgs {
   int64_t n;
   Packed xform, grad, jgrad;
   const float* dcost;
-  int kstride;  // float4 per thread in sK (2J rounded up to odd)
-  int gbuf;     // bytes of one warp's staging buffer (32 rows), 0 if unstaged
 };
 
-__host__ __device__ inline void carve_bw(Bump& b, const BwArgs& a, RobotSm& rb, uint8_t*& gbuf_all,
-                                         uint64_t*& bars, float4*& sK) {
-  gbuf_all = b.take<uint8_t>((size_t)BW_WARPS * a.gbuf);
-  bars = b.take<uint64_t>(BW_WARPS);
+__host__ __device__ inline void carve_bw(Bump& b, const BwArgs& a, RobotSm& rb, uint8_t*& ring,
+                                         float4*& sK, float*& sQ) {
+  ring = b.take<uint8_t>((size_t)BW_WARPS * SEG_SLOTS * SEG_BYTES);
   carve_robot(b, a.r.J, a.r.S, rb);
-  sK = b.take<float4>((size_t)BW_BLOCK * a.kstride);
+  sK = b.take<float4>((size_t)BW_BLOCK * 2 * a.r.J);  // per warp [2J][32 lanes]
+  sQ = b.take<float>((size_t)BW_WARPS * 2 * 32 * a.r.J);  // two q tiles per warp
 }
 
+// One warp's view of its gradient rows through the segment ring.  Every
+// lane holds the same copy of the bookkeeping (all calls are warp-uniform).
+// A segment holds 12k values (k per word) of each row, i.e. spheres
+// 4k c .. 4k c + 4k - 1 of segment c, so a sphere's three values never
+// straddle two segments; the spheres must come in increasing index order.
+//
+// A segment of the warp's 32 rows is 96 chunks of 16 bytes; lane m copies
+// chunks m, m + 32 and m + 64 (chunk i: row i / 3, third i % 3 of the
+// segment row) with cp.async, so each copy instruction reads whole runs of
+// about 11 consecutive rows and the slot fills linearly.  Every segment is
+// one commit group of each lane, and every release commits one group (empty
+// past the last segment), so waiting until at most SEG_SLOTS - 1 groups are
+// pending always means the segment in hand has landed.
+struct SegReader {
+  uint8_t* slots;       // this warp's [SEG_SLOTS][32 rows][SEG_W words]
+  const uint8_t* rows;  // the gradient rows
+  int64_t stride, n;    // row stride (bytes), rows
+  int nseg, lane, kw;   // segments per tile, lane, values per word
+  int64_t first, step;  // this warp's first tile and tile stride
+  int64_t total;        // segments of all this warp's tiles
+  int64_t g0 = 0;       // global index of the current tile's segment 0
+  int64_t issued = 0;   // segments issued so far
+  int cur = -1;         // segment of the current tile in hand, -1: none
+  int s_end = 0;        // first sphere past the segment in hand
+  const uint32_t* row = nullptr;  // this lane's row in the slot in hand
+
+  __device__ __forceinline__ void issue_next() {  // warp-uniform
+    const int64_t gi = issued++;
+    if (gi < total) {
+      const int64_t kk = gi / nseg;
+      const int sg = (int)(gi - kk * nseg);
+      const int64_t r0 = (first + kk * step) * 32;
+      uint8_t* slot = slots + (gi % SEG_SLOTS) * SEG_BYTES;
+      const int64_t col = (int64_t)sg * SEG_W * 4;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int i = lane + 32 * t, r = i / 3, third = i - 3 * r;
+        const int64_t off = col + 16 * third;
+        if (r0 + r < n && off < stride)  // rows past n and past the row's end stay as they are
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                           (uint32_t)__cvta_generic_to_shared(slot + 16 * i)),
+                       "l"(rows + (r0 + r) * stride + off)
+                       : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  __device__ __forceinline__ void start() {
+    for (int i = 0; i < SEG_SLOTS; ++i) issue_next();
+  }
+  __device__ __forceinline__ void acquire(int c) {
+    const int64_t gs = g0 + c;
+    row = reinterpret_cast<const uint32_t*>(slots + (gs % SEG_SLOTS) * SEG_BYTES) + lane * SEG_W;
+    s_end = 4 * kw * (c + 1);
+    asm volatile("cp.async.wait_group %0;" ::"n"(SEG_SLOTS - 1) : "memory");
+    __syncwarp();  // every lane's copies of this segment are visible
+  }
+  __device__ __forceinline__ void release() {
+    __syncwarp();  // every lane is done reading the slot
+    issue_next();
+  }
+  __device__ __forceinline__ void advance_to(int c) {
+    while (cur < c) {
+      if (cur >= 0) release();
+      ++cur;
+      acquire(cur);
+    }
+  }
+  __device__ __forceinline__ void end_tile() {
+    advance_to(nseg - 1);
+    release();
+    g0 += nseg;
+    cur = -1;
+    s_end = 0;
+  }
+  __device__ __forceinline__ void finish() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+  // The three values of sphere s: one segment check, then one 32-bit
+  // shared load per value.
+  template <int K>
+  __device__ __forceinline__ void sphere(int s, const DevFmt& f, float& g0_, float& g1_, float& g2_) {
+    if (s >= s_end) advance_to(s / (4 * kw));
+    const int base = 12 * kw * cur;  // first value of the segment
+    float v[3];
+    if constexpr (K == KIND_F32) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[d] = __uint_as_float(row[3 * s + d - base]);
+    } else {
+      int k = kw;
+      if constexpr (K != KIND_GENERIC) k = Fmt<K>::k;
+      const int i0 = 3 * s - base;
+      int w = i0 / k, r = i0 - w * k;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const uint32_t word = row[w];
+        if constexpr (K == KIND_GENERIC) {
+          v[d] = decode_generic((word >> (f.bits * r)) & f.mask, f);
+        } else {
+          constexpr int b = Fmt<K>::bits;
+          v[d] = dec_pair<K>((word >> (b * r)) & ((1u << b) - 1u), 0u).x;
+        }
+        if (++r == k) {
+          r = 0;
+          ++w;
+        }
+      }
+    }
+    g0_ = v[0];
+    g1_ = v[1];
+    g2_ = v[2];
+  }
+};
+
 // GK: format kind of the gradient rows (the hot input), fixed at compile time.
-// STAGED: rows come through the TMA staging buffer, else straight from global.
-template <int GK, bool STAGED>
-__global__ void __launch_bounds__(BW_BLOCK) backward_kernel(BwArgs a) {
+template <int GK>
+__global__ void __launch_bounds__(BW_BLOCK, 4) backward_kernel(BwArgs a) {
   extern __shared__ float4 smem4[];
   const int J = a.r.J;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Bump b(smem4);
   RobotSm rb;
-  uint8_t* gbuf_all;
-  uint64_t* bars;
+  uint8_t* ring;
   float4* sK;
-  carve_bw(b, a, rb, gbuf_all, bars, sK);
+  float* sQ;
+  carve_bw(b, a, rb, ring, sK, sQ);
   load_robot(a.r, rb);
-  uint8_t* gbuf = gbuf_all + warp * a.gbuf;
-  uint64_t* bar = bars + warp;
-  if (STAGED && lane == 0) mbar_init(bar, 1);
   __syncthreads();
+  int in_order = 1;  // spheres grouped by link in increasing link order
+  for (int k = threadIdx.x; k < a.r.S; k += blockDim.x) in_order &= rb.order[k] == k;
+  const bool use_ring = __syncthreads_and(in_order);
 
-  float4* myK = sK + threadIdx.x * a.kstride;
-  uint32_t phase = 0;
+  float4* myK = sK + (size_t)warp * 2 * J * 32 + lane;  // term i at myK[32 i]
+  float* qbuf = sQ + (size_t)warp * 2 * 32 * J;
   const int64_t n_tiles = (a.n + 31) / 32;
-  for (int64_t tile = (int64_t)blockIdx.x * BW_WARPS + warp; tile < n_tiles;
-       tile += (int64_t)gridDim.x * BW_WARPS) {
-    const int64_t c0 = tile * 32;
-    const int rows = (int)(a.n - c0 < 32 ? a.n - c0 : 32);
-    if (STAGED && lane == 0) {  // stage the warp's gradient rows (contiguous in global)
-      const uint32_t bytes = (uint32_t)(rows * a.grad.stride);
-      mbar_expect_tx(bar, bytes);
-      bulk_g2s(gbuf, a.grad.ptr + c0 * a.grad.stride, bytes, bar);
+  const int64_t first = (int64_t)blockIdx.x * BW_WARPS + warp, step = (int64_t)gridDim.x * BW_WARPS;
+  const int64_t my_tiles = first < n_tiles ? (n_tiles - 1 - first) / step + 1 : 0;
+  SegReader sr;
+  sr.slots = ring + (size_t)warp * SEG_SLOTS * SEG_BYTES;
+  sr.rows = a.grad.ptr;
+  sr.stride = a.grad.stride;
+  sr.n = a.n;
+  sr.nseg = (int)((3 * a.r.S + 12 * a.grad.f.k - 1) / (12 * a.grad.f.k));
+  sr.lane = lane;
+  sr.kw = a.grad.f.k;
+  sr.first = first;
+  sr.step = step;
+  sr.total = use_ring ? my_tiles * sr.nseg : 0;
+  if (use_ring) sr.start();
+  if (a.q && my_tiles > 0) q_prefetch(qbuf, a.q, first * 32, a.n, J, lane);
+
+  for (int64_t k = 0; k < my_tiles; ++k) {
+    const int64_t c = (first + k * step) * 32 + lane;
+    const bool live = c < a.n;
+    const float* qp = nullptr;
+    if (a.q) {  // this tile's q rows, and the next tile's in flight
+      q_wait();
+      if (k + 1 < my_tiles) q_prefetch(qbuf + ((k + 1) & 1) * 32 * J, a.q, (first + (k + 1) * step) * 32, a.n, J, lane);
+      qp = qbuf + (k & 1) * 32 * J + lane * J;
     }
-    const int64_t c = c0 + lane;
-    const bool live = lane < rows;
-    RowReader<STAGED ? ROW_SHARED : ROW_GLOBAL_RO> g{
-        STAGED ? gbuf + lane * a.grad.stride
-               : (live ? a.grad.ptr + c * a.grad.stride : a.grad.ptr)};
-    RowReader<ROW_GLOBAL_RO> x{a.xform.ptr && live ? a.xform.ptr + c * a.xform.stride : nullptr};
     const float dc = live && a.dcost ? a.dcost[c] : 1.f;
-    const bool ok = backward_config<GK, STAGED ? ROW_SHARED : ROW_GLOBAL_RO>(
-        rb, J, live, a.q && live ? a.q + c * J : nullptr, x, a.xform.f, g, a.grad.f, dc, myK,
-        [&]() {
-          if (!STAGED) return true;
-          const bool done = mbar_wait(bar, phase);
-          if (__all_sync(FULL_MASK, done)) return true;
-          if (lane == 0) atomicCAS(&g_backward_error, 0, (int)VAPR_ERR_TIMEOUT);
-          mbar_wait(bar, phase);  // let the copy in flight land before leaving
-          return false;
-        });
-    if (!ok) return;
-    if (STAGED) phase ^= 1u;
-    if (live) backward_store(J, myK, a.jgrad.ptr + c * a.jgrad.stride, a.jgrad.stride, a.jgrad.f);
-    // every lane is done with the staged rows before the next copy overwrites them
-    __syncwarp();
-    if (STAGED) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    RowReader<ROW_GLOBAL_RO> x{a.xform.ptr && live ? a.xform.ptr + c * a.xform.stride : nullptr};
+    auto put = [&](int j, float v) { myK[32 * (2 * j + 1)].w = v; };  // after b_j is read
+    if (use_ring) {
+      backward_config<GK>(rb, J, live, qp, x, a.xform.f, sr, a.grad.f, dc, myK, 32, put);
+      sr.end_tile();
+    } else {
+      RowReader<ROW_GLOBAL_RO> g{live ? a.grad.ptr + c * a.grad.stride : a.grad.ptr};
+      backward_config<GK>(rb, J, live, qp, x, a.xform.f, g, a.grad.f, dc, myK, 32, put);
+    }
+    if (live)
+      backward_store(J, [&](int i) { return myK[32 * (2 * i + 1)].w; }, a.jgrad.ptr + c * a.jgrad.stride,
+                     a.jgrad.stride, a.jgrad.f);
+    __syncwarp();  // every lane is done with this tile's q rows
   }
+  sr.finish();
 }
 
 int backward_device_error(bool reset) {
@@ -156,6 +253,20 @@ int backward_device_error(bool reset) {
   return v;
 }
 
+static void (*bw_kernel_for(int kind))(BwArgs) {
+  switch (kind) {
+    case KIND_F32: return backward_kernel<KIND_F32>;
+    case KIND_F16: return backward_kernel<KIND_F16>;
+    case KIND_BF16: return backward_kernel<KIND_BF16>;
+    case KIND_E4M3: return backward_kernel<KIND_E4M3>;
+    case KIND_E5M2: return backward_kernel<KIND_E5M2>;
+    case KIND_E2M1: return backward_kernel<KIND_E2M1>;
+    case KIND_E3M2: return backward_kernel<KIND_E3M2>;
+    case KIND_E2M3: return backward_kernel<KIND_E2M3>;
+    default: return backward_kernel<KIND_GENERIC>;
+  }
+}
+
 cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform, Packed grad,
                             const float* dcost, int64_t n, Packed jgrad, cudaStream_t st) {
   BwArgs a;
@@ -166,38 +277,15 @@ cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform, Pa
   a.grad = grad;
   a.jgrad = jgrad;
   a.dcost = dcost;
-  a.kstride = (2 * r.J) | 1;
-  // Stage the rows through shared memory when a block's buffers fit at
-  // least one block per SM; otherwise stream them from global memory.
-  void (*kern)(BwArgs) = nullptr;
-  size_t smem = 0;
-  int per_sm = 0;
-  for (int staged = 1; staged >= 0 && per_sm <= 0; --staged) {
-    a.gbuf = staged ? (int)(32 * grad.stride) : 0;
-    Bump b(nullptr);
-    RobotSm rb;
-    uint8_t* gb;
-    uint64_t* bars;
-    float4* sK;
-    carve_bw(b, a, rb, gb, bars, sK);
-    smem = b.bytes();
-#define VAPR_BW_CASE(K) \
-  case K: kern = staged ? backward_kernel<K, true> : backward_kernel<K, false>; break;
-    switch (grad.f.kind) {
-      VAPR_BW_CASE(KIND_F32)
-      VAPR_BW_CASE(KIND_F16)
-      VAPR_BW_CASE(KIND_BF16)
-      VAPR_BW_CASE(KIND_E4M3)
-      VAPR_BW_CASE(KIND_E5M2)
-      VAPR_BW_CASE(KIND_E2M1)
-      VAPR_BW_CASE(KIND_E3M2)
-      VAPR_BW_CASE(KIND_E2M3)
-      default: kern = staged ? backward_kernel<KIND_GENERIC, true>
-                             : backward_kernel<KIND_GENERIC, false>;
-    }
-#undef VAPR_BW_CASE
-    per_sm = blocks_per_sm((const void*)kern, BW_BLOCK, smem);
-  }
+  void (*kern)(BwArgs) = bw_kernel_for(grad.f.kind);
+  Bump b(nullptr);
+  RobotSm rb;
+  uint8_t* ring;
+  float4* sK;
+  float* sQ;
+  carve_bw(b, a, rb, ring, sK, sQ);
+  const size_t smem = b.bytes();
+  const int per_sm = blocks_per_sm((const void*)kern, BW_BLOCK, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (n + 31) / 32;
   const int64_t blocks = (tiles + BW_WARPS - 1) / BW_WARPS;

@@ -197,10 +197,10 @@ __global__ void __launch_bounds__(BT_BLOCK) batched_kernel(BatchArgs a) {
       RowReader<ROW_GLOBAL_COHERENT> g{grow0 + r * P.grad_stride};
       RowReader<ROW_GLOBAL_RO> x{nullptr};
       float4* myK = sU + r * kstride;
-      backward_config<GK, ROW_GLOBAL_COHERENT>(rb, J, true, sQ + r * J, x, a.fJ, g, a.fG,
-                                               P.dcost ? P.dcost[c] : 1.f, myK,
-                                               [] { return true; });
-      backward_store(J, myK, P.jgrad + c * P.jgrad_stride, P.jgrad_stride, a.fJ);
+      backward_config<GK>(rb, J, true, sQ + r * J, x, a.fJ, g, a.fG, P.dcost ? P.dcost[c] : 1.f, myK, 1,
+                          [&](int j, float v) { myK[2 * j + 1].w = v; });
+      backward_store(J, [&](int i) { return myK[2 * i + 1].w; }, P.jgrad + c * P.jgrad_stride,
+                     P.jgrad_stride, a.fJ);
     }
     __syncthreads();
   }

@@ -17,7 +17,8 @@
 // fewer instructions than per-link candidate lists or a compacted queue of
 // surviving pairs: the bounding test is cheaper than the bookkeeping.)
 // With a broad-phase grid (grid.cuh) each sphere visits only the cuboids
-// listed for its cell, with the same tests in the same order.
+// listed for its cell (those it can penetrate) and runs the exact term on
+// them alone, in the same order.
 //
 // Self pairs: the block groups the pair table by cluster pair (runs of up to
 // three spheres of one link, load_self); per configuration, cluster pairs
@@ -27,8 +28,8 @@
 // Determinism: every sphere adds its terms in cuboid order in one register,
 // and a skipped pair would have added exactly zero, so the result of a
 // configuration does not depend on the batch it is in or on which pairs the
-// bounding test lets through.  Active self pairs are applied sphere-major in
-// table order; which lane sums a pair's penetration follows from the
+// bounding test lets through.  Active self pairs are applied one at a time
+// in table order; which lane sums a pair's penetration follows from the
 // configuration's own kept cluster pairs.
 #include <map>
 #include <mutex>
@@ -116,19 +117,32 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
   const int64_t c_end = a.slot >= 0 ? a.n : (c_begin + per_block < a.n ? c_begin + per_block : a.n);
   if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
+  auto draw = [&]() -> unsigned int {  // lane 0's ticket (the other lanes get 0)
+    if (lane != 0) return 0u;
+    return a.slot >= 0 ? atomicAdd(&g_sched[a.slot].next, 1u) : (unsigned int)atomicAdd(&s_next, 1);
+  };
+  unsigned int k_next = draw();
   for (;;) {
-    unsigned int k = 0;
-    if (lane == 0) k = a.slot >= 0 ? atomicAdd(&g_sched[a.slot].next, 1u) : (unsigned int)atomicAdd(&s_next, 1);
-    k = __shfl_sync(0xffffffffu, k, 0);
+    const unsigned int k = __shfl_sync(0xffffffffu, k_next, 0);
     const int64_t c = c_begin + k;
     if (c >= c_end) break;
+    // the next ticket is drawn now and read after this configuration: its
+    // latency overlaps this configuration's work
+    k_next = draw();
     out.cost = a.cost ? a.cost + c : nullptr;
     out.dist = a.dist.ptr ? reinterpret_cast<uint32_t*>(a.dist.ptr + c * a.dist.stride) : nullptr;
     out.grad = a.grad.ptr ? reinterpret_cast<uint32_t*>(a.grad.ptr + c * a.grad.stride) : nullptr;
+    // between the environment and self terms (the next ticket is back by
+    // then): lanes prefetch the next configuration's P row into L1
+    auto prefetch_next = [&]() {
+      const int64_t cn = c_begin + __shfl_sync(0xffffffffu, k_next, 0);
+      if (cn < c_end && 128 * lane < a.pos.stride)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.pos.ptr + cn * a.pos.stride + 128 * lane));
+    };
     collision_config<false, MASKED>(a.r, a.sc.O, rb, sm, w,
                                     reinterpret_cast<const uint32_t*>(a.pos.ptr + c * a.pos.stride),
                                     a.pos.f, a.dist.f, a.grad.f, a.eta, a.w_c, a.w_s, out, lane,
-                                    MASKED ? a.est + c * a.r.S : nullptr, a.margin, grid, cells);
+                                    MASKED ? a.est + c * a.r.S : nullptr, a.margin, grid, cells, prefetch_next);
   }
   if (a.slot >= 0) {  // every warp of this block has drawn its last ticket
     __syncthreads();

@@ -62,6 +62,9 @@ cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc,
 cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform,
                             Packed grad, const float* dcost, int64_t n,
                             Packed jgrad, cudaStream_t st);
+cudaError_t launch_fused(const RobotArgs& r, const SceneArgs& sc, const vapr_cost_params& p, const float* q,
+                         const float* dcost, int64_t n, const vapr_format_table& t, float* cost, Packed dist,
+                         Packed jgrad, cudaStream_t st);
 cudaError_t launch_pack(const float* src, int64_t rows, int64_t row_len, Packed dst,
                         cudaStream_t st);
 cudaError_t launch_unpack(Packed src, int64_t rows, int64_t row_len, float* dst,

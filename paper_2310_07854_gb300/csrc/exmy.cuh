@@ -49,6 +49,8 @@ struct DevFmt {
   uint32_t max_code, inf_code, nan_code;
   int ovf_inf;            // overflow -> Inf (IEEE without saturation)
   int ieee, fn;
+  int fastdec;            // finite-only, all codes numeric, E < 8: decode by one multiply
+  float dec_scale;        // 2^(127 - bias)
 };
 
 // ------------------------------------------------------------ generic path
@@ -85,6 +87,14 @@ __device__ __forceinline__ uint32_t encode_generic(float x, const DevFmt& f) {
 
 __device__ __forceinline__ float decode_generic(uint32_t code, const DevFmt& f) {
   const uint32_t s = ((code >> (f.E + f.M)) & 1u) << 31;
+  if (f.fastdec) {
+    // The code's exponent and mantissa fields placed at float32's mantissa
+    // point read as 2^(e - 127) (1 + m 2^-M) (e > 0) or m 2^(-126 - M)
+    // (e = 0); times 2^(127 - bias) that is the format's value, normal or
+    // subnormal, exactly (E < 8 keeps every value a normal float32 or zero).
+    const uint32_t mag = code & ((1u << (f.E + f.M)) - 1u);
+    return __uint_as_float(__float_as_uint(__uint_as_float(mag << (23 - f.M)) * f.dec_scale) | s);
+  }
   const uint32_t ef = (code >> f.M) & f.all_e;
   const uint32_t mf = code & f.all_m;
   if (f.ieee && ef == f.all_e) return __uint_as_float(mf ? 0x7fc00000u : (s | 0x7f800000u));

@@ -2,128 +2,247 @@
 // Sec. III-B): joint configurations -> link transforms -> sphere centres,
 // stored in the ExMy format of out_spheres (Sec. III-C).
 //
-// A block takes tiles of FK_TILE configurations, with two kinds of warps
-// and two transform buffers: FK_PRODUCERS warps (one configuration per
-// thread) run the joint chains of a tile (fk_chain) into one buffer while
-// FK_WRITERS warps write the packed rows of the previous tile from the other
-// one (fk_store_pos_staged: lanes take spheres, then words).  The hand-over
-// uses named barriers: a buffer's FULL barrier (producers arrive, writers
-// wait) and its EMPTY barrier (writers arrive, producers wait before
-// refilling it); both sides walk the same tiles, so every arrival has its
-// matching wait and no wait can be left open.  (Measured on GB300, 2^20
-// configurations of the particle arm: with the per-word row writer of an
-// earlier version the writers were the bottleneck and this split did not
-// pay; with the staged writer the chains are.)
+// The kernel is bound by writing the packed P rows (624 bytes per
+// configuration in float32), so it is laid out around the stores.  One
+// thread per configuration; a warp owns tiles of 32 consecutive
+// configurations, whose P rows are one contiguous range of global memory.
+// The q rows of the warp's next tile are copied into shared memory
+// (cp.async) while it works on the current one.
+//
+// A thread walks the spheres in index order and keeps one link transform
+// in registers, advancing the joint chain (joint_step) when a sphere's link
+// is further down the chain, and restarting it from the base when a
+// sphere's link is nearer the base (only for robots whose spheres are not
+// grouped by link); all lanes walk the same spheres, so the branches are
+// warp-uniform.  No transform is stored.  The thread packs its row one
+// segment at a time: a segment is PSEG_W = 12 words of the row, i.e. 4k
+// spheres for k values per word, packed in registers with every bit position
+// fixed at compile time (for k <= 2; for k >= 3 three words at a time), and
+// written into its row of the warp's shared tile (rows an odd number of
+// 16-byte chunks apart: conflict-free 16-byte stores).  The tile's 32 rows
+// are one contiguous range of global memory, so the warp then copies them
+// out as whole lines, lane i taking 16-byte chunk i, i + 32, ...  (Writing
+// 48-byte pieces of 32 rows at a time, by a 2-D TMA store per segment or by
+// plain stores, was measured first: about 2.2 TB/s in float32 either way.)
+// The segments cover the padded row, so padding words are written as zero.
+//
+// With the optional transform rows T (table->xform), each thread also keeps
+// its transforms in shared memory and writes its T row from there.
 #include "stages.cuh"
 
 namespace vapr {
 
-constexpr int FK_TILE = 128;
-constexpr int FK_PRODUCERS = FK_TILE / 32;
-constexpr int FK_WRITERS = 12;
-constexpr int FK_THREADS = 32 * (FK_PRODUCERS + FK_WRITERS);
-constexpr int BAR_PROD = 1, BAR_FULL = 2, BAR_EMPTY = 4;  // named barriers (0: __syncthreads)
+constexpr int FK_WARPS = 2;
+constexpr int FK_BLOCK = 32 * FK_WARPS;
+constexpr int PSEG_W = 12;     // words of each row per segment (48 B)
+static_assert(PSEG_W == 12, "a segment holds 12k values = 4k whole spheres");
 
 struct FkArgs {
   RobotArgs r;
   const float* q;
   int64_t n;
   Packed pos, xform;
-  int tstride;    // float4 per configuration in the transform tile (3J rounded up to odd)
-  int stage_len;  // floats of a writer warp's staging row
+  int tstride;  // float4 per thread of transform rows (3J rounded up to odd), 0 without T
+  int nseg;     // segments per (padded) P row
+  int pitch;    // bytes per row in the warp's shared tile: >= 48 nseg, an odd number of 16-byte chunks
 };
 
-// stage_len: floats of a writer warp's staging row (the packed row's words, >= 3S)
-__host__ __device__ inline void carve_fk(Bump& b, int J, int S, int tstride, int stage_len, RobotSm& rb,
-                                         float4*& sT, float*& sQ, float*& sStage) {
-  carve_robot(b, J, S, rb);
-  sT = b.take<float4>((size_t)2 * FK_TILE * tstride);  // two buffers
-  sQ = b.take<float>((size_t)FK_TILE * J);
-  sStage = b.take<float>((size_t)FK_WRITERS * stage_len);
+__host__ __device__ inline void carve_fk(Bump& b, const FkArgs& a, RobotSm& rb, uint8_t*& tiles,
+                                         float*& sQ, float4*& sT) {
+  tiles = b.take<uint8_t>((size_t)FK_WARPS * 32 * a.pitch);  // 32 rows per warp
+  carve_robot(b, a.r.J, a.r.S, rb);
+  sQ = b.take<float>((size_t)FK_WARPS * 2 * 32 * a.r.J);  // two q tiles per warp
+  sT = b.take<float4>((size_t)FK_BLOCK * a.tstride);
 }
 
-template <int ID, int COUNT>
-__device__ __forceinline__ void bar_sync() {
-  asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
-}
-template <int ID, int COUNT>
-__device__ __forceinline__ void bar_arrive() {
-  asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
-}
-__device__ __forceinline__ void full_arrive(int buf) {
-  if (buf) bar_arrive<BAR_FULL + 1, FK_THREADS>(); else bar_arrive<BAR_FULL, FK_THREADS>();
-}
-__device__ __forceinline__ void full_wait(int buf) {
-  if (buf) bar_sync<BAR_FULL + 1, FK_THREADS>(); else bar_sync<BAR_FULL, FK_THREADS>();
-}
-__device__ __forceinline__ void empty_arrive(int buf) {
-  if (buf) bar_arrive<BAR_EMPTY + 1, FK_THREADS>(); else bar_arrive<BAR_EMPTY, FK_THREADS>();
-}
-__device__ __forceinline__ void empty_wait(int buf) {
-  if (buf) bar_sync<BAR_EMPTY + 1, FK_THREADS>(); else bar_sync<BAR_EMPTY, FK_THREADS>();
+// One packed word from KW values v[0..KW-1] (compile-time positions);
+// the same codes and bit layout as pack_word_t.
+template <int PK, int KW>
+__device__ __forceinline__ uint32_t enc_word(const float* v, const DevFmt& f) {
+  if constexpr (PK == KIND_F32) {
+    return __float_as_uint(v[0]);
+  } else if constexpr (PK == KIND_GENERIC) {
+    uint32_t w = 0u;
+#pragma unroll
+    for (int j = 0; j < KW; ++j) w |= (encode_generic(v[j], f) & f.mask) << (f.bits * j);
+    return w;
+  } else {
+    constexpr int b = Fmt<PK>::bits;
+    static_assert(Fmt<PK>::k == KW, "values per word of the kind");
+    uint32_t w = 0u;
+#pragma unroll
+    for (int j = 0; j < KW; j += 2) {
+      uint32_t pr = enc_pair<PK>(v[j], j + 1 < KW ? v[j + 1] : 0.f, f);
+      if (j + 1 >= KW) pr &= (1u << b) - 1u;
+      w |= pr << (b * j);
+    }
+    return w;
+  }
 }
 
-__global__ void __launch_bounds__(FK_THREADS, 2) fk_kernel(FkArgs a) {
+// A thread's walk over its configuration's spheres: the transform of link
+// cl in (R, t), advanced (or restarted) on demand.
+struct ChainWalk {
+  float R[3][3], t[3];
+  int cl;
+  __device__ __forceinline__ void reset() {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) R[a][b] = a == b ? 1.f : 0.f;
+      t[a] = 0.f;
+    }
+    cl = -1;
+  }
+  // to link l (warp-uniform); every transform computed goes to myT (if any)
+  __device__ __forceinline__ void to(const RobotSm& rb, int l, const float* q, float4* myT) {
+    if (l < cl) reset();
+    while (cl < l) {
+      ++cl;
+      joint_step(rb, cl, q[cl], R, t);
+      if (myT) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) myT[3 * cl + k] = make_float4(R[k][0], R[k][1], R[k][2], t[k]);
+      }
+    }
+  }
+  __device__ __forceinline__ void centre(const float4& p, float* v) const {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = fmaf(R[k][0], p.x, fmaf(R[k][1], p.y, fmaf(R[k][2], p.z, t[k])));
+  }
+};
+
+// Values of spheres s0 .. s0+ns-1 (compile-time ns) into v[3 ns]; zeros past
+// the last sphere.
+template <int NS>
+__device__ __forceinline__ void sphere_values(const RobotSm& rb, int S, int s0, ChainWalk& cw, const float* q,
+                                              float4* myT, float* v) {
+#pragma unroll
+  for (int u = 0; u < NS; ++u) {
+    const int s = s0 + u;
+    if (s < S) {
+      const int l = rb.link0[s];
+      if (l != cw.cl) cw.to(rb, l, q, myT);
+      cw.centre(rb.sph[s], v + 3 * u);
+    } else {
+      v[3 * u] = v[3 * u + 1] = v[3 * u + 2] = 0.f;
+    }
+  }
+}
+
+// PK: format kind of P; KW: its values per word, both fixed at compile time.
+// XF: the transform rows are written too.
+template <int PK, int KW, bool XF>
+__global__ void __launch_bounds__(FK_BLOCK) fk_kernel(FkArgs a) {
   extern __shared__ float4 smem4[];
   const int J = a.r.J, S = a.r.S;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Bump b(smem4);
   RobotSm rb;
+  uint8_t* tiles;
+  float* sQ;
   float4* sT;
-  float *sQ, *sStage;
-  carve_fk(b, J, S, a.tstride, a.stage_len, rb, sT, sQ, sStage);
+  carve_fk(b, a, rb, tiles, sQ, sT);
   load_robot(a.r, rb);
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t n_tiles = (a.n + FK_TILE - 1) / FK_TILE;
-  const int my_tiles = blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-  const size_t buf_len = (size_t)FK_TILE * a.tstride;
 
-  if (warp < FK_PRODUCERS) {
-    const int t = threadIdx.x;
-    for (int k = 0; k < my_tiles; ++k) {
-      const int64_t base = (blockIdx.x + (int64_t)k * gridDim.x) * FK_TILE;
-      const int rows = (int)(a.n - base < FK_TILE ? a.n - base : FK_TILE);
-      bar_sync<BAR_PROD, 32 * FK_PRODUCERS>();  // the previous chains are done with sQ
-      for (int i = t; i < rows * J; i += 32 * FK_PRODUCERS) sQ[i] = a.q[base * J + i];
-      bar_sync<BAR_PROD, 32 * FK_PRODUCERS>();
-      if (k >= 2) empty_wait(k & 1);  // the writers are done with this buffer
-      if (t < rows) fk_chain(rb, J, sQ + t * J, sT + (k & 1) * buf_len + t * a.tstride);
-      full_arrive(k & 1);
+  float4* myT = XF ? sT + threadIdx.x * a.tstride : nullptr;
+  uint8_t* tb = tiles + (size_t)warp * 32 * a.pitch;  // this warp's 32 rows
+  uint4* myrow = reinterpret_cast<uint4*>(tb + (size_t)lane * a.pitch);
+  float* qbuf = sQ + (size_t)warp * 2 * 32 * J;
+  const int cpr = (int)(a.pos.stride / 16);  // 16-byte chunks per row
+  const int64_t n_tiles = (a.n + 31) / 32;
+  const int64_t first = (int64_t)blockIdx.x * FK_WARPS + warp, step = (int64_t)gridDim.x * FK_WARPS;
+  if (first < n_tiles) q_prefetch(qbuf, a.q, first * 32, a.n, J, lane);
+  int buf = 0;
+  for (int64_t tile = first; tile < n_tiles; tile += step, buf ^= 1) {
+    q_wait();  // this tile's q rows
+    if (tile + step < n_tiles) q_prefetch(qbuf + (buf ^ 1) * 32 * J, a.q, (tile + step) * 32, a.n, J, lane);
+    const int64_t c = tile * 32 + lane;
+    const bool live = c < a.n;
+    const float* myq = qbuf + buf * 32 * J + lane * J;  // (rows past n: zeros, never stored)
+    ChainWalk cw;
+    cw.reset();
+    for (int g = 0; g < a.nseg; ++g) {
+      if constexpr (KW <= 2) {  // all 4 KW spheres of the segment at once
+        float v[12 * KW];
+        sphere_values<4 * KW>(rb, S, 4 * KW * g, cw, myq, myT, v);
+        uint32_t wd[PSEG_W];
+#pragma unroll
+        for (int w = 0; w < PSEG_W; ++w) wd[w] = enc_word<PK, KW>(v + w * KW, a.pos.f);
+        myrow[3 * g] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        myrow[3 * g + 1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        myrow[3 * g + 2] = make_uint4(wd[8], wd[9], wd[10], wd[11]);
+      } else {  // KW spheres -> 3 words at a time
+        uint32_t* dst = reinterpret_cast<uint32_t*>(myrow + 3 * g);
+        for (int sb = 0; sb < 4; ++sb) {
+          float v[3 * KW];
+          sphere_values<KW>(rb, S, (4 * g + sb) * KW, cw, myq, myT, v);
+#pragma unroll
+          for (int w = 0; w < 3; ++w) dst[3 * sb + w] = enc_word<PK, KW>(v + w * KW, a.pos.f);
+        }
+      }
     }
-    for (int k = my_tiles - 2 > 0 ? my_tiles - 2 : 0; k < my_tiles; ++k)
-      empty_wait(k & 1);  // the writers' last two hand-backs
-  } else {
-    const int wr = warp - FK_PRODUCERS;
-    float* stage = sStage + wr * a.stage_len;
-    for (int i = 3 * S + lane; i < a.stage_len; i += 32) stage[i] = 0.f;  // padding words stay zero
     __syncwarp();
-    for (int k = 0; k < my_tiles; ++k) {
-      const int64_t base = (blockIdx.x + (int64_t)k * gridDim.x) * FK_TILE;
-      const int rows = (int)(a.n - base < FK_TILE ? a.n - base : FK_TILE);
-      const float4* T = sT + (k & 1) * buf_len;
-      full_wait(k & 1);
-      {
-        const int words = (int)(a.pos.stride / 4);
-        dispatch_kind(a.pos.f.kind, [&](auto kc) {
-          constexpr int K = decltype(kc)::value;
-          for (int r = wr; r < rows; r += FK_WRITERS)
-            fk_store_pos_staged<K>(rb, S, T + r * a.tstride,
-                                   reinterpret_cast<uint32_t*>(a.pos.ptr + (base + r) * a.pos.stride),
-                                   words, a.pos.f, lane, stage);
-        });
+    {  // the tile's rows are one contiguous range: lanes take its 16-byte chunks in order
+      const int rows = (int)(a.n - tile * 32 < 32 ? a.n - tile * 32 : 32);
+      uint4* out = reinterpret_cast<uint4*>(a.pos.ptr + tile * 32 * a.pos.stride);
+      int r = lane / cpr, ch = lane - r * cpr;  // chunk i = r cpr + ch, i = lane + 32 t
+      const int dr = 32 / cpr, dc = 32 - dr * cpr;
+      for (int i = lane; i < rows * cpr; i += 32) {
+        out[i] = reinterpret_cast<const uint4*>(tb + (size_t)r * a.pitch)[ch];
+        r += dr;
+        ch += dc;
+        if (ch >= cpr) {
+          ch -= cpr;
+          ++r;
+        }
       }
-      if (a.xform.ptr) {
-        const int words = (int)(a.xform.stride / 4);
-        dispatch_kind(a.xform.f.kind, [&](auto kc) {
-          constexpr int K = decltype(kc)::value;
-          for (int r = wr; r < rows; r += FK_WRITERS)
-            fk_store_xform<K>(J, T + r * a.tstride,
-                              reinterpret_cast<uint32_t*>(a.xform.ptr + (base + r) * a.xform.stride),
-                              words, a.xform.f, lane);
-        });
-      }
-      empty_arrive(k & 1);
     }
+    if constexpr (XF) {  // every joint's transform, then the packed T row
+      cw.to(rb, J - 1, myq, myT);
+      __syncwarp();
+      if (live) {  // element e of T_j is value 12 j + e
+        uint4* out = reinterpret_cast<uint4*>(a.xform.ptr + c * a.xform.stride);
+        const int chunks = (int)(a.xform.stride / 16);
+        for (int cc = 0; cc < chunks; ++cc)
+          out[cc] = pack_chunk_dyn(cc, 12 * J, a.xform.f, [&](int i) {
+            const int j = i / 12, e = i - 12 * j;
+            const int d = e < 9 ? e / 3 : e - 9;
+            const int col = e < 9 ? e - 3 * d : 3;
+            const float4 row = myT[3 * j + d];
+            return col == 0 ? row.x : col == 1 ? row.y : col == 2 ? row.z : row.w;
+          });
+      }
+    }
+    __syncwarp();  // the rows are copied out and this tile's q rows read before they are reused
+  }
+}
+
+using FkKernel = void (*)(FkArgs);
+
+template <bool XF>
+static FkKernel fk_kernel_for(const DevFmt& f) {
+  switch (f.kind) {
+    case KIND_F32: return fk_kernel<KIND_F32, 1, XF>;
+    case KIND_F16: return fk_kernel<KIND_F16, 2, XF>;
+    case KIND_BF16: return fk_kernel<KIND_BF16, 2, XF>;
+    case KIND_E4M3: return fk_kernel<KIND_E4M3, 4, XF>;
+    case KIND_E5M2: return fk_kernel<KIND_E5M2, 4, XF>;
+    case KIND_E2M1: return fk_kernel<KIND_E2M1, 8, XF>;
+    case KIND_E3M2: return fk_kernel<KIND_E3M2, 5, XF>;
+    case KIND_E2M3: return fk_kernel<KIND_E2M3, 5, XF>;
+    default:
+      switch (f.k) {
+        case 1: return fk_kernel<KIND_GENERIC, 1, XF>;
+        case 2: return fk_kernel<KIND_GENERIC, 2, XF>;
+        case 3: return fk_kernel<KIND_GENERIC, 3, XF>;
+        case 4: return fk_kernel<KIND_GENERIC, 4, XF>;
+        case 5: return fk_kernel<KIND_GENERIC, 5, XF>;
+        case 6: return fk_kernel<KIND_GENERIC, 6, XF>;
+        case 8: return fk_kernel<KIND_GENERIC, 8, XF>;
+        default: return nullptr;
+      }
   }
 }
 
@@ -135,20 +254,26 @@ cudaError_t launch_fk(const RobotArgs& r, const float* q, int64_t n, Packed pos,
   a.n = n;
   a.pos = pos;
   a.xform = xform;
-  a.tstride = (3 * r.J) | 1;  // odd float4 stride: conflict-free 16-byte stores
-  a.stage_len = (int)(pos.stride / 4) > 3 * r.S ? (int)(pos.stride / 4) : 3 * r.S;
-  a.stage_len = (a.stage_len + 3) & ~3;
+  const bool xf = xform.ptr != nullptr;
+  a.tstride = xf ? (3 * r.J) | 1 : 0;  // odd float4 stride: conflict-free 16-byte accesses
+  const int64_t words = pos.stride / 4;
+  a.nseg = (int)((words + PSEG_W - 1) / PSEG_W);
+  a.pitch = 16 * ((3 * a.nseg) | 1);  // odd chunk count: conflict-free 16-byte row stores
+  const FkKernel kern = xf ? fk_kernel_for<true>(pos.f) : fk_kernel_for<false>(pos.f);
+  if (!kern) return cudaErrorInvalidValue;
   Bump b(nullptr);
   RobotSm rb;
+  uint8_t* ring;
+  float* sQ;
   float4* sT;
-  float *sQ, *sStage;
-  carve_fk(b, r.J, r.S, a.tstride, a.stage_len, rb, sT, sQ, sStage);
+  carve_fk(b, a, rb, ring, sQ, sT);
   const size_t smem = b.bytes();
-  const int per_sm = blocks_per_sm((const void*)fk_kernel, FK_THREADS, smem);
+  const int per_sm = blocks_per_sm((const void*)kern, FK_BLOCK, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-  const int64_t tiles = (n + FK_TILE - 1) / FK_TILE;
+  const int64_t tiles = (n + 31) / 32;
+  const int64_t blocks = (tiles + FK_WARPS - 1) / FK_WARPS;
   const int64_t cap = (int64_t)sm_count() * per_sm;
-  fk_kernel<<<(int)(tiles < cap ? tiles : cap), FK_THREADS, smem, st>>>(a);
+  kern<<<(int)(blocks < cap ? blocks : cap), FK_BLOCK, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -6,10 +6,12 @@
 // by the requested cells per axis.  Then a thread per (cell, 64-bit chunk)
 // sets bit b when the cell, widened by a thousandth of its side, comes
 // within 1.0001 R + 1e-5 m of cuboid 64 k + b's centre (R its grown
-// bounding radius).  The widening covers the rounding of the cell index the
-// collision stage computes, and the factor the float32 rounding of both
-// distance tests, so a sphere's cell lists every cuboid whose bounding test
-// can pass for it.
+// bounding radius) and the box distance from the cell's centre to the
+// cuboid, less the cell's half diagonal, is below reach + eta + 2 SLACK.
+// The widening covers the rounding of the cell index the collision stage
+// computes, the factor and SLACK the float32 rounding of the distance
+// tests; the box distance is 1-Lipschitz, so a sphere's cell lists every
+// cuboid whose bounding test can pass for it and that it can penetrate.
 #include <cmath>
 
 #include "stages.cuh"
@@ -111,19 +113,34 @@ __global__ void __launch_bounds__(256) grid_fill_kernel(GridBuild a) {
       bmin[d] = g.lo[d] + (float)idx[d] * g.h - widen;
       bmax[d] = g.lo[d] + (float)(idx[d] + 1) * g.h + widen;
     }
+    // the widened cell's centre and half diagonal
+    float cc[3];
+    for (int d = 0; d < 3; ++d) cc[d] = 0.5f * (bmin[d] + bmax[d]);
+    const float hd = 0.8660254f * (g.h + 2.f * widen);
+    const float near = a.reach + a.eta + hd + 2.f * SLACK;
     unsigned long long bits = 0ull;
     for (int b = 0; b < 64; ++b) {
       const int o = 64 * k + b;
       if (o >= a.sc.O) break;
       const float R = grid_reach_of(a.sc, o, a.eta, a.reach);
+      const float* P = a.sc.pose + 12 * o;
       float d2 = 0.f;
       for (int d = 0; d < 3; ++d) {
-        const float c = a.sc.pose[12 * o + 9 + d];
+        const float c = P[9 + d];
         const float e = fmaxf(fmaxf(bmin[d] - c, c - bmax[d]), 0.f);
         d2 = fmaf(e, e, d2);
       }
       const float thr = fmaf(R, 1.0001f, 1e-5f);
-      if (d2 < thr * thr) bits |= 1ull << b;
+      if (!(d2 < thr * thr)) continue;
+      // box distance at the cell centre; the distance is 1-Lipschitz, so no
+      // point of the cell is nearer than that minus the half diagonal
+      const float dx = cc[0] - P[9], dy = cc[1] - P[10], dz = cc[2] - P[11];
+      float u[3];
+      for (int e = 0; e < 3; ++e)  // x_e = (R^T (c - t))_e, R row-major
+        u[e] = fabsf(fmaf(P[e], dx, fmaf(P[3 + e], dy, P[6 + e] * dz))) - a.sc.half[3 * o + e];
+      const float v0 = fmaxf(u[0], 0.f), v1 = fmaxf(u[1], 0.f), v2 = fmaxf(u[2], 0.f);
+      const float dbox = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2))) + fminf(fmaxf(u[0], fmaxf(u[1], u[2])), 0.f);
+      if (dbox < near) bits |= 1ull << b;
     }
     a.out[t] = make_uint2((uint32_t)bits, (uint32_t)(bits >> 32));
   }

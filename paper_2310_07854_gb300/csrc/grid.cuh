@@ -1,12 +1,13 @@
 // Broad-phase grid of a scene: a uniform grid of cubic cells over the
 // region where any sphere can touch a cuboid's bounding sphere, each cell
-// holding the bitmask of the cuboids whose bounding test a sphere centred
-// in that cell can pass.  It is scene preprocessing (grid.cu builds it) and
-// only narrows which cuboids the environment loop visits: the loop still
-// runs the same bounding test and the same exact distance, in cuboid order,
-// on the cuboids it visits, and a cuboid left out of a cell is one whose
-// bounding test fails for every sphere in it, so the results are the same
-// as the plain loop over all cuboids, bit for bit.
+// holding the bitmask of the cuboids that a sphere centred in that cell can
+// both pass the bounding test of and penetrate (grid.cu: a bounding-sphere
+// test and a box-distance test of the cell).  It is scene preprocessing and
+// only narrows which cuboids the environment loop visits: the loop runs the
+// same exact distance, in cuboid order, on the cuboids it visits, and a
+// cuboid left out of a cell is one that no sphere in it penetrates (its
+// term would be exactly zero), so the results are the same as the plain
+// loop over all cuboids, bit for bit.
 //
 // Layout (device memory, 16-byte aligned):
 //   GridHeader (GRID_HEADER_BYTES), then cells[dims_z][dims_y][dims_x] of

@@ -123,32 +123,57 @@ __device__ inline void load_clusters(int J, int S, const RobotSm& r) {
 }
 
 // ------------------------------------------------------------ FK (thread)
+// One step of the joint chain: (R, t) = T_{j-1} becomes T_j = T_{j-1} F_j Rz(q_j).
+__device__ __forceinline__ void joint_step(const RobotSm& r, int j, float qj, float (&R)[3][3], float (&t)[3]) {
+  const float4 f0 = r.F[3 * j], f1 = r.F[3 * j + 1], f2 = r.F[3 * j + 2];
+  float B[3][3], tb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {  // T_{j-1} F_j
+    B[k][0] = fmaf(R[k][0], f0.x, fmaf(R[k][1], f1.x, R[k][2] * f2.x));
+    B[k][1] = fmaf(R[k][0], f0.y, fmaf(R[k][1], f1.y, R[k][2] * f2.y));
+    B[k][2] = fmaf(R[k][0], f0.z, fmaf(R[k][1], f1.z, R[k][2] * f2.z));
+    tb[k] = fmaf(R[k][0], f0.w, fmaf(R[k][1], f1.w, fmaf(R[k][2], f2.w, t[k])));
+  }
+  float sn, cs;
+  sincosf(qj, &sn, &cs);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {  // ... Rz(q_j)
+    R[k][0] = fmaf(cs, B[k][0], sn * B[k][1]);
+    R[k][1] = fmaf(cs, B[k][1], -sn * B[k][0]);
+    R[k][2] = B[k][2];
+    t[k] = tb[k];
+  }
+}
+
 // The joint chain of one configuration into myT: 3 float4 per joint, rows
 // (R_d0, R_d1, R_d2, t_d).
 __device__ __forceinline__ void fk_chain(const RobotSm& r, int J, const float* q, float4* myT) {
   float R[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
   float t[3] = {0.f, 0.f, 0.f};
   for (int j = 0; j < J; ++j) {
-    const float4 f0 = r.F[3 * j], f1 = r.F[3 * j + 1], f2 = r.F[3 * j + 2];
-    float B[3][3], tb[3];
+    joint_step(r, j, q[j], R, t);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {  // T_{j-1} F_j
-      B[k][0] = fmaf(R[k][0], f0.x, fmaf(R[k][1], f1.x, R[k][2] * f2.x));
-      B[k][1] = fmaf(R[k][0], f0.y, fmaf(R[k][1], f1.y, R[k][2] * f2.y));
-      B[k][2] = fmaf(R[k][0], f0.z, fmaf(R[k][1], f1.z, R[k][2] * f2.z));
-      tb[k] = fmaf(R[k][0], f0.w, fmaf(R[k][1], f1.w, fmaf(R[k][2], f2.w, t[k])));
-    }
-    float sn, cs;
-    sincosf(q[j], &sn, &cs);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {  // ... Rz(q_j)
-      R[k][0] = fmaf(cs, B[k][0], sn * B[k][1]);
-      R[k][1] = fmaf(cs, B[k][1], -sn * B[k][0]);
-      R[k][2] = B[k][2];
-      t[k] = tb[k];
-      myT[3 * j + k] = make_float4(R[k][0], R[k][1], R[k][2], t[k]);
-    }
+    for (int k = 0; k < 3; ++k) myT[3 * j + k] = make_float4(R[k][0], R[k][1], R[k][2], t[k]);
   }
+}
+
+// The q rows of configurations c0 .. c0+31 into dst (32 x J floats,
+// row-major): rows below n by 4-byte asynchronous copies (cp.async),
+// committed as one group of this thread, rows past n as zeros; q_wait makes
+// them visible to the warp.
+__device__ __forceinline__ void q_prefetch(float* dst, const float* q, int64_t c0, int64_t n, int J, int lane) {
+  const int rows = (int)(n - c0 < 32 ? n - c0 : 32);
+  const float* src = q + c0 * J;
+  for (int i = lane; i < rows * J; i += 32)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + i)),
+                 "l"(src + i)
+                 : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int i = rows * J + lane; i < 32 * J; i += 32) dst[i] = 0.f;
+}
+__device__ __forceinline__ void q_wait() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
 }
 
 // Packed sphere-centre row of one configuration from its transforms T;
@@ -163,48 +188,6 @@ __device__ __forceinline__ void fk_store_pos(const RobotSm& r, int S, const floa
       const float4 row = T[3 * r.link0[s] + d];
       const float4 p = r.sph[s];
       return fmaf(row.x, p.x, fmaf(row.y, p.y, fmaf(row.z, p.z, row.w)));
-    });
-}
-
-// The same row through a per-warp float staging row (stage: `words` floats,
-// 16-byte aligned, words 3S.. zero): lanes take spheres, so the three
-// centre values of a sphere share one read of its transform rows; then
-// lanes take the words, FP32 rows as 16-byte copies.  The values are those
-// of fk_store_pos, bit for bit.
-template <int K>
-__device__ __forceinline__ void fk_store_pos_staged(const RobotSm& r, int S, const float4* T, uint32_t* out,
-                                                    int words, const DevFmt& f, int lane, float* stage) {
-  for (int s = lane; s < S; s += 32) {
-    const int l = r.link0[s];
-    const float4 p = r.sph[s];
-    const float4 r0 = T[3 * l], r1 = T[3 * l + 1], r2 = T[3 * l + 2];
-    stage[3 * s] = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
-    stage[3 * s + 1] = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
-    stage[3 * s + 2] = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
-  }
-  __syncwarp();
-  if constexpr (K == KIND_F32) {
-    for (int c = lane; c < words / 4; c += 32)
-      reinterpret_cast<uint4*>(out)[c] = reinterpret_cast<const uint4*>(stage)[c];
-  } else {
-    const int nv = 3 * S;
-    for (int w = lane; w < words; w += 32) out[w] = pack_word_t<K>(w, nv, f, [&](int i) { return stage[i]; });
-  }
-  __syncwarp();
-}
-
-// Packed link-transform row (element e of T_j is value 12 j + e).
-template <int K>
-__device__ __forceinline__ void fk_store_xform(int J, const float4* T, uint32_t* out, int words,
-                                               const DevFmt& f, int lane) {
-  const int nv = 12 * J;
-  for (int w = lane; w < words; w += 32)
-    out[w] = pack_word_t<K>(w, nv, f, [&](int i) {
-      const int j = i / 12, e = i - 12 * j;
-      const int d = e < 9 ? e / 3 : e - 9;
-      const int col = e < 9 ? e - 3 * d : 3;
-      const float4 row = T[3 * j + d];
-      return col == 0 ? row.x : col == 1 ? row.y : col == 2 ? row.z : row.w;
     });
 }
 
@@ -381,45 +364,16 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
 }
 
 // One warp's working set for one configuration.
-constexpr int ACT_CAP = 64;  // warp list of active self pairs awaiting their gradient update
-
 struct CollWarp {
   float4* P;       // [S] (x, y, z, r)
   float4* acc;     // [S] (D, gx, gy, gz)
-  float4* act;     // [ACT_CAP] active self pairs: (bits of i | j << 16, u) with u = w_s (c_i - c_j)/|c_i - c_j|
   float4* cls;     // [NC] cluster bounding spheres of this configuration (centre, radius)
 };
 
 __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp& w) {
   w.P = b.take<float4>(S);
   w.acc = b.take<float4>(S);
-  w.act = b.take<float4>(ACT_CAP);
   w.cls = b.take<float4>(cluster_bound(S, J));
-}
-
-// Applies the listed active self pairs to acc, sphere-major: each lane takes
-// its spheres (up to two per 64) and walks the list in order, subtracting u
-// where it is the pair's first sphere and adding it where it is the second,
-// so every sphere receives its self terms in list order (the order in which
-// self_pairs tested them: the cluster-pair table's order).
-__device__ __forceinline__ void apply_self_pairs(const CollWarp& w, int S, int n_act, int lane) {
-  for (int base = 0; base < S; base += 64) {
-    const int sa = base + lane, sb = sa + 32;
-    float4 a = sa < S ? w.acc[sa] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 b = sb < S ? w.acc[sb] : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int e = 0; e < n_act; ++e) {
-      const float4 t = w.act[e];
-      const uint32_t ij = __float_as_uint(t.x);
-      const int i = (int)(ij & 0xffffu), j = (int)(ij >> 16);
-      if (i == sa) { a.y -= t.y; a.z -= t.z; a.w -= t.w; }
-      if (j == sa) { a.y += t.y; a.z += t.z; a.w += t.w; }
-      if (i == sb) { b.y -= t.y; b.z -= t.z; b.w -= t.w; }
-      if (j == sb) { b.y += t.y; b.z += t.z; b.w += t.w; }
-    }
-    if (sa < S) w.acc[sa] = a;
-    if (sb < S) w.acc[sb] = b;
-  }
-  __syncwarp();
 }
 
 // Radii into P[].w and zero accumulators (once per robot).
@@ -431,10 +385,11 @@ __device__ __forceinline__ void init_coll_warp(const RobotArgs& r, const CollWar
 }
 
 // Exact sphere-cuboid term: penetration max(0, r + eta - d) of the sphere
-// (c, c.w = r) against cuboid o, and its gradient -w_c grad d, added to acc
-// (x: D, yzw: G).  Zero when the sphere is clear of the cuboid.
-__device__ __forceinline__ void box_term(const SceneSm& m, int o, const float4& c, float eta, float w_c,
-                                         float4& acc) {
+// (c, c.w = r) against cuboid o, and its gradient -w_c grad d, as
+// (D, gx, gy, gz); all zero when the sphere is clear of the cuboid.
+__device__ __forceinline__ float4 box_term_value(const SceneSm& m, int o, const float4& c, float eta,
+                                                 float w_c) {
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 A0 = m.cubA[3 * o], A1 = m.cubA[3 * o + 1], A2 = m.cubA[3 * o + 2];
   const float4 H = m.cubH[o];
   const float dx = c.x - A0.w, dy = c.y - A1.w, dz = c.z - A2.w;
@@ -457,11 +412,27 @@ __device__ __forceinline__ void box_term(const SceneSm& m, int o, const float4& 
     const float l0 = outside ? s0 * v0 * inv : (k == 0 ? s0 : 0.f);
     const float l1 = outside ? s1 * v1 * inv : (k == 1 ? s1 : 0.f);
     const float l2 = outside ? s2 * v2 * inv : (k == 2 ? s2 : 0.f);
-    acc.x += pen;  // gradient of the hinge: -grad d, scaled by w_coll
-    acc.y += -w_c * fmaf(A0.x, l0, fmaf(A1.x, l1, A2.x * l2));
-    acc.z += -w_c * fmaf(A0.y, l0, fmaf(A1.y, l1, A2.y * l2));
-    acc.w += -w_c * fmaf(A0.z, l0, fmaf(A1.z, l1, A2.z * l2));
+    acc.x = pen;  // gradient of the hinge: -grad d, scaled by w_coll
+    acc.y = -w_c * fmaf(A0.x, l0, fmaf(A1.x, l1, A2.x * l2));
+    acc.z = -w_c * fmaf(A0.y, l0, fmaf(A1.y, l1, A2.y * l2));
+    acc.w = -w_c * fmaf(A0.z, l0, fmaf(A1.z, l1, A2.z * l2));
   }
+  return acc;
+}
+
+// The term added to acc (x: D, yzw: G) when the sphere penetrates the cuboid.
+__device__ __forceinline__ void add_term(float4& acc, const float4& t) {
+  if (t.x > 0.f) {
+    acc.x += t.x;
+    acc.y += t.y;
+    acc.z += t.z;
+    acc.w += t.w;
+  }
+}
+
+__device__ __forceinline__ void box_term(const SceneSm& m, int o, const float4& c, float eta, float w_c,
+                                         float4& acc) {
+  add_term(acc, box_term_value(m, o, c, eta, w_c));
 }
 
 struct CollOut {
@@ -493,10 +464,10 @@ __device__ __forceinline__ void load_centres(const uint32_t* prow, const DevFmt&
   });
 }
 
-// Cost (w_c sum_s acc[s].x + extra), the packed D (acc.x) and G (acc.yzw)
-// rows of one configuration, one word per lane; then zeroes acc.
-__device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const DevFmt& fD, const DevFmt& fG,
-                                             float w_c, float extra, const CollOut& out, int lane) {
+// Cost (w_c sum_s acc[s].x + extra) and the packed D row (acc.x) of one
+// configuration, one word per lane.
+__device__ __forceinline__ void coll_cost_dist(const CollWarp& w, int S, const DevFmt& fD, float w_c, float extra,
+                                               const CollOut& out, int lane) {
   float local = 0.f;
   for (int s = lane; s < S; s += 32) local += w.acc[s].x;
   local = w_c * local + extra;
@@ -510,6 +481,20 @@ __device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const Dev
         out.dist[wd] = pack_word_t<K>(wd, S, fD, [&](int i) { return w.acc[i].x; });
     });
   }
+}
+
+// Zeroes acc for the next configuration.
+__device__ __forceinline__ void coll_reset(const CollWarp& w, int S, int lane) {
+  __syncwarp();
+  for (int s = lane; s < S; s += 32) w.acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncwarp();
+}
+
+// Cost, the packed D (acc.x) and G (acc.yzw) rows of one configuration, one
+// word per lane; then zeroes acc.
+__device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const DevFmt& fD, const DevFmt& fG,
+                                             float w_c, float extra, const CollOut& out, int lane) {
+  coll_cost_dist(w, S, fD, w_c, extra, out, lane);
   if (out.grad) {
     const int nv = 3 * S;
     dispatch_kind(fG.kind, [&](auto kc) {
@@ -521,9 +506,7 @@ __device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const Dev
         });
     });
   }
-  __syncwarp();
-  for (int s = lane; s < S; s += 32) w.acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncwarp();
+  coll_reset(w, S, lane);
 }
 
 // Environment terms of sphere p over the cuboids obase + b for the set bits
@@ -543,6 +526,22 @@ __device__ __forceinline__ void env_bits(const SceneSm& m, int obase, unsigned l
   }
 }
 
+// Environment terms of sphere p over the cuboids obase + b for the set bits
+// b of mm (a scene-grid cell's candidates), in increasing cuboid order: the
+// exact term alone.  A candidate of the grid's cell is one the sphere can
+// penetrate, and a pair the bounding test would reject has a negative
+// penetration (SLACK), so the sums equal the plain loop's bit for bit.
+__device__ __forceinline__ void env_bits_direct(const SceneSm& m, int obase, unsigned long long mm,
+                                                const float4& p, float eta, float w_c, float4& acc) {
+  while (__any_sync(FULL_MASK, mm != 0ull)) {
+    if (mm != 0ull) {
+      const int o = obase + __ffsll((long long)mm) - 1;
+      mm &= mm - 1ull;
+      box_term(m, o, p, eta, w_c, acc);
+    }
+  }
+}
+
 // Self-collision of one configuration (P in w.P, acc receiving gradients):
 // returns this lane's share of the penetration sum.
 //
@@ -554,8 +553,8 @@ __device__ __forceinline__ void env_bits(const SceneSm& m, int obase, unsigned l
 // (A NaN anywhere keeps the cluster pair.)  The kept cluster pairs of each
 // 32 are expanded into their pairs through a warp prefix sum of their pair
 // counts (lane t of a chunk finds its cluster pair by binary search), and
-// the pairs are tested in table order; active pairs are listed and applied
-// sphere-major in that order.
+// the pairs are tested in table order; each active pair's gradient is added
+// to its two spheres in that order, one pair at a time.
 __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m, const CollWarp& w,
                                             int S, float w_s, int lane) {
   const int NC = rb.n_cl[0], NG = m.self_meta[0];
@@ -583,7 +582,6 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
   }
   __syncwarp();
   float selfsum = 0.f;
-  int n_act = 0;
   for (int g0 = 0; g0 < NG; g0 += 32) {
     const int g = g0 + lane;
     int cnt = 0, st = 0;
@@ -629,28 +627,41 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
           uz = dz * inv;
         }
       }
-      const unsigned am = __ballot_sync(FULL_MASK, act);
-      if (act) {  // list the active pair (table order = lane order within the chunk)
-        selfsum += pen;
-        w.act[n_act + __popc(am & ((1u << lane) - 1u))] =
-            make_float4(__uint_as_float((uint32_t)i | ((uint32_t)j << 16)), ux, uy, uz);
-      }
-      n_act += __popc(am);
-      if (n_act > ACT_CAP - 32) {  // the next chunk might not fit: apply what is listed
+      // active pairs in table order (lane order within the chunk), one at a
+      // time: the pair's own lane updates both spheres' gradients, so every
+      // sphere receives its self terms in that order
+      unsigned am = __ballot_sync(FULL_MASK, act);
+      if (act) selfsum += pen;
+      while (am) {
+        const int e = __ffs(am) - 1;
+        am &= am - 1u;
+        if (lane == e) {
+          float4 ai = w.acc[i];
+          ai.y -= ux;
+          ai.z -= uy;
+          ai.w -= uz;
+          w.acc[i] = ai;
+          float4 aj = w.acc[j];
+          aj.y += ux;
+          aj.z += uy;
+          aj.w += uz;
+          w.acc[j] = aj;
+        }
         __syncwarp();
-        apply_self_pairs(w, S, n_act, lane);
-        n_act = 0;
       }
     }
   }
   __syncwarp();
-  if (n_act > 0) apply_self_pairs(w, S, n_act, lane);
+  (void)S;
   return selfsum;
 }
 
 // Environment terms of sphere p (when v) over the candidates of its grid cell.
 // first: the cell's first mask chunk, already loaded (the caller issues the
 // loads of both its spheres' first chunks before either loop starts).
+// DIRECT runs the exact term on the candidates alone (env_bits_direct),
+// else the bounding test first (env_bits).
+template <bool DIRECT>
 __device__ __forceinline__ void env_grid(const SceneSm& m, const GridHeader& g, const uint2* c,
                                          uint2 first, const float4& p, float eta, float w_c, float4& acc) {
   for (int k = 0; k < (g.words >> 1); ++k) {
@@ -658,12 +669,14 @@ __device__ __forceinline__ void env_grid(const SceneSm& m, const GridHeader& g, 
     unsigned long long mm = ((unsigned long long)wd.y << 32) | wd.x;
     const int left = g.O - 64 * k;  // bits past the last cuboid stay clear
     if (left < 64) mm &= left > 0 ? (1ull << left) - 1ull : 0ull;
-    env_bits(m, 64 * k, mm, p, eta, w_c, acc);
+    if constexpr (DIRECT) env_bits_direct(m, 64 * k, mm, p, eta, w_c, acc);
+    else env_bits(m, 64 * k, mm, p, eta, w_c, acc);
   }
 }
 
 // Environment terms of spheres pa and pb (when va, vb) over their cells'
 // candidates.
+template <bool DIRECT = false>
 __device__ __forceinline__ void env_grid2(const SceneSm& m, const GridHeader& g, const uint2* cells,
                                           bool va, const float4& pa, bool vb, const float4& pb, float eta,
                                           float w_c, float4& acca, float4& accb) {
@@ -671,8 +684,8 @@ __device__ __forceinline__ void env_grid2(const SceneSm& m, const GridHeader& g,
   const uint2* cb = vb ? grid_cell(g, cells, pb) : nullptr;
   const uint2 fa = ca ? __ldg(ca) : make_uint2(0u, 0u);
   const uint2 fb = cb ? __ldg(cb) : make_uint2(0u, 0u);
-  env_grid(m, g, ca, fa, pa, eta, w_c, acca);
-  env_grid(m, g, cb, fb, pb, eta, w_c, accb);
+  env_grid<DIRECT>(m, g, ca, fa, pa, eta, w_c, acca);
+  env_grid<DIRECT>(m, g, cb, fb, pb, eta, w_c, accb);
 }
 
 // The whole collision stage of one configuration by one warp: P row in,
@@ -682,21 +695,25 @@ __device__ __forceinline__ void env_grid2(const SceneSm& m, const GridHeader& g,
 // read-only cache.  MASKED takes a per-sphere distance estimate `est` (this
 // configuration's row): spheres with est - r >= margin skip the cuboid
 // tests.
-template <bool COHERENT = false, bool MASKED = false>
-__device__ __forceinline__ void collision_config(const RobotArgs& r, int O, const RobotSm& rb,
-                                                 const SceneSm& m, const CollWarp& w,
-                                                 const uint32_t* prow, const DevFmt& fP,
-                                                 const DevFmt& fD, const DevFmt& fG, float eta,
-                                                 float w_c, float w_s, const CollOut& out,
-                                                 int lane, const float* est = nullptr,
-                                                 float margin = 0.f,
+// The environment and self terms of one configuration by one warp, on the
+// centres in w.P: per-sphere penetration and gradient in w.acc (D, G);
+// returns this lane's share of the self-penetration sum.  MASKED takes a
+// per-sphere distance estimate `est` (this configuration's row): spheres
+// with est - r >= margin skip the cuboid tests.
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// between(): called by every lane after the environment terms, before the
+// self terms (the collision kernel prefetches its next row there).
+template <bool MASKED = false, typename Between = NoHook>
+__device__ __forceinline__ float collision_terms(const RobotArgs& r, int O, const RobotSm& rb, const SceneSm& m,
+                                                 const CollWarp& w, float eta, float w_c, float w_s, int lane,
+                                                 const float* est = nullptr, float margin = 0.f,
                                                  const GridHeader* grid = nullptr,
-                                                 const uint2* cells = nullptr) {
+                                                 const uint2* cells = nullptr, Between between = Between{}) {
   const int S = r.S;
-  // ---- 1. sphere centres (one word per lane)
-  load_centres<COHERENT>(prow, fP, S, w.P, lane);
-  __syncwarp();
-  // ---- 2. environment, sphere-major: lane owns spheres base + lane and
+  // ---- environment, sphere-major: lane owns spheres base + lane and
   //      base + 32 + lane and sums their terms in registers, cuboid by
   //      cuboid in order.  A sphere takes cuboid o's exact test only when it
   //      lies within the cuboid's bounding sphere grown by r + eta (+ SLACK);
@@ -712,7 +729,7 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
     }
     float4 acca = make_float4(0.f, 0.f, 0.f, 0.f), accb = acca;
     if (grid) {  // broad phase: each sphere visits its cell's candidates only
-      env_grid2(m, *grid, cells, va, pa, vb, pb, eta, w_c, acca, accb);
+      env_grid2<true>(m, *grid, cells, va, pa, vb, pb, eta, w_c, acca, accb);
     } else if (__any_sync(FULL_MASK, va || vb)) {
 #pragma unroll 2  // measured at 40 cuboids: 4.68 ns per configuration unrolled by 1, 4.59 by 2, 4.74 by 4
       for (int o = 0; o < O; ++o) {
@@ -731,11 +748,35 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
     if (sb < S) w.acc[sb] = accb;
   }
   __syncwarp();
-  // ---- 4. self-collision: cluster bounding spheres, then the pairs of the
+  between();
+  // ---- self-collision: cluster bounding spheres, then the pairs of the
   //      cluster pairs whose spheres can touch (self_pairs)
-  const float selfsum = self_pairs(rb, m, w, S, w_s, lane);
+  return self_pairs(rb, m, w, S, w_s, lane);
+}
+
+// The whole collision stage of one configuration by one warp: P row in,
+// cost, D and G rows out (see collision.cu for the scheme).
+// COHERENT reads the P row with loads that see writes made earlier in the
+// same kernel (the fused multi-problem kernel); otherwise through the
+// read-only cache.
+template <bool COHERENT = false, bool MASKED = false, typename Between = NoHook>
+__device__ __forceinline__ void collision_config(const RobotArgs& r, int O, const RobotSm& rb,
+                                                 const SceneSm& m, const CollWarp& w,
+                                                 const uint32_t* prow, const DevFmt& fP,
+                                                 const DevFmt& fD, const DevFmt& fG, float eta,
+                                                 float w_c, float w_s, const CollOut& out,
+                                                 int lane, const float* est = nullptr,
+                                                 float margin = 0.f,
+                                                 const GridHeader* grid = nullptr,
+                                                 const uint2* cells = nullptr, Between between = Between{}) {
+  // ---- 1. sphere centres (one word per lane)
+  load_centres<COHERENT>(prow, fP, r.S, w.P, lane);
+  __syncwarp();
+  // ---- 2.-4. environment and self terms
+  const float selfsum =
+      collision_terms<MASKED>(r, O, rb, m, w, eta, w_c, w_s, lane, est, margin, grid, cells, between);
   // ---- 5. cost and packed outputs, then reset acc
-  coll_outputs(w, S, fD, fG, w_c, w_s * selfsum, out, lane);
+  coll_outputs(w, r.S, fD, fG, w_c, w_s * selfsum, out, lane);
 }
 
 // ------------------------------------------------------- backward (thread)
@@ -769,22 +810,28 @@ struct RowReader {
   __device__ __forceinline__ float value_k(int i, const DevFmt& f) {  // compile-time format
     return row_value<K>(i, f, [&](int w) { return word(w); });
   }
+  // the three values of sphere s (values 3s .. 3s+2)
+  template <int K>
+  __device__ __forceinline__ void sphere(int s, const DevFmt& f, float& g0, float& g1, float& g2) {
+    g0 = value_k<K>(3 * s, f);
+    g1 = value_k<K>(3 * s + 1, f);
+    g2 = value_k<K>(3 * s + 2, f);
+  }
 };
 
-// Joint gradient of one configuration into myK[2j+1].w (times dc).
+// Joint gradient of one configuration: put(j, dc * J_j) for j < J, with the
+// per-joint terms (a_j, K_j), (b_j, -) in myK[0], myK[kst], .. myK[(2J-1) kst].
 // live == false runs the same control flow without touching memory.
-// before_spheres() is called once, by every lane, before the first gradient
-// value is read; returning false aborts (the function returns false).
-template <int GK, int GSRC, typename Before>
-__device__ __forceinline__ bool backward_config(const RobotSm& rb, int J, bool live,
-                                                const float* q, RowReader<ROW_GLOBAL_RO>& x,
-                                                const DevFmt& fx, RowReader<GSRC>& g,
-                                                const DevFmt& fg, float dc, float4* myK,
-                                                Before before_spheres) {
+// The gradient reader g gives the three values of a sphere (g.sphere); all
+// lanes of a warp ask for the same sphere at the same time (the sphere
+// order is the robot's, shared by all lanes).
+template <int GK, typename XR, typename GR, typename Put>
+__device__ __forceinline__ void backward_config(const RobotSm& rb, int J, bool live, const float* q, XR& x,
+                                                const DevFmt& fx, GR& g, const DevFmt& fg, float dc,
+                                                float4* myK, int kst, Put put) {
   float R[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
   float t[3] = {0.f, 0.f, 0.f};
   float F0 = 0.f, F1 = 0.f, F2 = 0.f, M0 = 0.f, M1 = 0.f, M2 = 0.f;
-  bool staged = false;
   for (int j = 0; j < J; ++j) {
     if (live) {
       if (x.row) {  // stored transforms: element e of T_j is value 12j + e
@@ -795,24 +842,7 @@ __device__ __forceinline__ bool backward_config(const RobotSm& rb, int J, bool l
           t[k] = x.value(12 * j + 9 + k, fx);
         }
       } else {  // recompute T_j = T_{j-1} F_j Rz(q_j)
-        const float4 f0 = rb.F[3 * j], f1 = rb.F[3 * j + 1], f2 = rb.F[3 * j + 2];
-        float B[3][3], tb[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          B[k][0] = fmaf(R[k][0], f0.x, fmaf(R[k][1], f1.x, R[k][2] * f2.x));
-          B[k][1] = fmaf(R[k][0], f0.y, fmaf(R[k][1], f1.y, R[k][2] * f2.y));
-          B[k][2] = fmaf(R[k][0], f0.z, fmaf(R[k][1], f1.z, R[k][2] * f2.z));
-          tb[k] = fmaf(R[k][0], f0.w, fmaf(R[k][1], f1.w, fmaf(R[k][2], f2.w, t[k])));
-        }
-        float sn, cs;
-        sincosf(q[j], &sn, &cs);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          R[k][0] = fmaf(cs, B[k][0], sn * B[k][1]);
-          R[k][1] = fmaf(cs, B[k][1], -sn * B[k][0]);
-          R[k][2] = B[k][2];
-          t[k] = tb[k];
-        }
+        joint_step(rb, j, q[j], R, t);
       }
     }
     // axis a_j, b_j = a_j x o_j, and the correction K_j
@@ -821,19 +851,14 @@ __device__ __forceinline__ bool backward_config(const RobotSm& rb, int J, bool l
     const float by = az * t[0] - ax * t[2];
     const float bz = ax * t[1] - ay * t[0];
     const float K = (ax * M0 + ay * M1 + az * M2) - (bx * F0 + by * F1 + bz * F2);
-    myK[2 * j] = make_float4(ax, ay, az, K);
-    myK[2 * j + 1] = make_float4(bx, by, bz, 0.f);
-    if (!staged && rb.start[j + 1] > rb.start[j]) {
-      if (!before_spheres()) return false;
-      staged = true;
-    }
-    if (live) {  // spheres on link j: F += G, M += c x G
-      for (int idx = rb.start[j]; idx < rb.start[j + 1]; ++idx) {
-        const int s = rb.order[idx];
-        const float g0 = g.template value_k<GK>(3 * s, fg);
-        const float g1 = g.template value_k<GK>(3 * s + 1, fg);
-        const float g2 = g.template value_k<GK>(3 * s + 2, fg);
-        if (g0 == 0.f && g1 == 0.f && g2 == 0.f) continue;
+    myK[2 * j * kst] = make_float4(ax, ay, az, K);
+    myK[(2 * j + 1) * kst] = make_float4(bx, by, bz, 0.f);
+    // spheres on link j: F += G, M += c x G (zero gradients add nothing)
+    for (int idx = rb.start[j]; idx < rb.start[j + 1]; ++idx) {
+      const int s = rb.order[idx];
+      float g0, g1, g2;
+      g.template sphere<GK>(s, fg, g0, g1, g2);
+      if (live && (g0 != 0.f || g1 != 0.f || g2 != 0.f)) {
         const float4 p = rb.sph[s];
         const float c0 = fmaf(R[0][0], p.x, fmaf(R[0][1], p.y, fmaf(R[0][2], p.z, t[0])));
         const float c1 = fmaf(R[1][0], p.x, fmaf(R[1][1], p.y, fmaf(R[1][2], p.z, t[1])));
@@ -847,22 +872,20 @@ __device__ __forceinline__ bool backward_config(const RobotSm& rb, int J, bool l
       }
     }
   }
-  if (!staged && !before_spheres()) return false;
   for (int j = 0; j < J; ++j) {
-    const float4 ak = myK[2 * j], b = myK[2 * j + 1];
+    const float4 ak = myK[2 * j * kst], b = myK[(2 * j + 1) * kst];
     const float Jj = (ak.x * M0 + ak.y * M1 + ak.z * M2) - (b.x * F0 + b.y * F1 + b.z * F2) - ak.w;
-    myK[2 * j + 1].w = dc * Jj;
+    put(j, dc * Jj);
   }
-  return true;
 }
 
-// Packed joint-gradient row from myK (padding words written as zero).
-__device__ __forceinline__ void backward_store(int J, const float4* myK, uint8_t* row, int64_t stride,
+// Packed joint-gradient row of J values get(i) (padding words written as zero).
+template <typename Get>
+__device__ __forceinline__ void backward_store(int J, Get get, uint8_t* row, int64_t stride,
                                                const DevFmt& fj) {
   uint4* out = reinterpret_cast<uint4*>(row);
   const int chunks = (int)(stride / 16);
-  for (int cc = 0; cc < chunks; ++cc)
-    out[cc] = pack_chunk_dyn(cc, J, fj, [&](int i) { return myK[2 * i + 1].w; });
+  for (int cc = 0; cc < chunks; ++cc) out[cc] = pack_chunk_dyn(cc, J, fj, get);
 }
 
 }  // namespace vapr

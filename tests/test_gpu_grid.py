@@ -1,10 +1,12 @@
 """The broad-phase grid of a scene (vapr_scene_grid_build): the collision
 stage gives the same bits with and without it, the cell of every point lists
-each cuboid whose bounding test can pass there, a grid that does not match
-the scene, eta or radii is ignored, and a matching one is the grid the
-kernel reads."""
+each cuboid that a sphere centred there can penetrate (box distance below
+reach + eta, from the FP64 oracle), a grid that does not match the scene,
+eta or radii is ignored, and a matching one is the grid the kernel reads."""
 import numpy as np
 import pytest
+
+import oracle
 
 from paper_2310_07854_gb300 import binding as B
 from paper_2310_07854_gb300 import formats as F
@@ -93,31 +95,35 @@ def cell_bits(hdr, cells, p):
 
 
 @pytest.mark.parametrize("cells_n", [3, 24, 64])
-def test_grid_lists_every_passing_cuboid(cells_n):
-    """Points spread over the region and points just inside the grown
-    bounding sphere of a cuboid: wherever |p - t_o| < r + R_o for some
-    radius r <= reach, the cell of p lists o."""
+def test_grid_lists_every_cuboid_a_sphere_can_penetrate(cells_n):
+    """Points spread over the region and points around each cuboid, many of
+    them near the threshold: wherever the box distance d_o(p) < reach + eta
+    (some sphere of radius <= reach centred at p penetrates o with margin
+    eta), the cell of p lists o."""
     w = synth.make_workload("particle_32768")
     sd = B.DeviceScene(w.scene)
     reach, eta = reach_of(w.robot), w.params.eta
     sd.build_grid(reach, eta, cells_n)
     hdr, cells = decode_grid(sd.grid)
     assert hdr["magic"] == 0x56475244 and hdr["O"] == w.scene.n_cuboids
-    half = np.asarray(w.scene.half_ext, np.float64).reshape(-1, 3)
-    cen = np.asarray(w.scene.pose, np.float64).reshape(-1, 12)[:, 9:12]
-    R = np.sqrt((half ** 2).sum(1)) + eta + 1e-4
+    pose = np.asarray(w.scene.pose, np.float32).reshape(-1, 12)
+    half = np.asarray(w.scene.half_ext, np.float32).reshape(-1, 3)
+    O = pose.shape[0]
     rng = np.random.default_rng(cells_n)
     lo = hdr["lo"].astype(np.float64)
     hi = lo + hdr["dims"] * hdr["h"]
     pts = [rng.uniform(lo - 0.1, hi + 0.1, size=(4000, 3))]
-    for o in range(len(R)):  # shells just inside and outside the grown sphere
-        d = rng.normal(size=(60, 3))
-        d /= np.linalg.norm(d, axis=1, keepdims=True)
-        s = (R[o] + reach) * rng.uniform(0.98, 1.001, size=(60, 1))
-        pts.append(cen[o] + d * s)
+    for o in range(O):  # around cuboid o, out to beyond the threshold
+        ext = np.abs(pose[o, :9].reshape(3, 3)).astype(np.float64) @ half[o] + reach + eta + 0.03
+        pts.append(pose[o, 9:12] + rng.uniform(-1, 1, size=(300, 3)) * ext)
     pts = np.concatenate(pts).astype(np.float32)
-    dist = np.linalg.norm(pts[:, None, :].astype(np.float64) - cen[None], axis=2)
-    must = dist < (R[None] + reach) * (1 - 1e-6)
+    m = pts.shape[0]
+    d = np.empty((m, O))
+    for o in range(O):
+        d[:, o] = oracle.box_sdf(np.repeat(pose[o:o + 1], m, 0), np.repeat(half[o:o + 1], m, 0), pts)[0]
+    must = d < (reach + eta) * (1 - 1e-6)
+    near = (np.abs(d - (reach + eta)) < 0.01) & must
+    assert near.sum() > 200  # many pairs close to the threshold
     checked = 0
     for p, row in zip(pts, must):
         if not row.any():
