@@ -422,10 +422,13 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
   Packed grad = packed(ws + align256((size_t)pos.stride * (size_t)n), 3 * (int64_t)r.S, table->grad);
   Packed none = packed(nullptr, 12 * (int64_t)r.J, table->xform);
   cudaError_t e = launch_fk(r, q, n, pos, none, s);
+  // the collision and backward kernels may load their tables while the
+  // stage before them finishes (programmatic dependent launch)
   if (e == cudaSuccess)
-    e = launch_collision(r, sc, *params, pos, n, cost, packed(dist_packed, r.S, table->dist), grad, s);
+    e = launch_collision(r, sc, *params, pos, n, cost, packed(dist_packed, r.S, table->dist), grad, s,
+                         nullptr, 0.f, true);
   if (e == cudaSuccess)
-    e = launch_backward(r, q, none, grad, dcost, n, packed(jgrad_packed, r.J, table->jgrad), s);
+    e = launch_backward(r, q, none, grad, dcost, n, packed(jgrad_packed, r.J, table->jgrad), s, true);
   return cuda_status(e);
 }
 

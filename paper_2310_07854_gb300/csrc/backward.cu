@@ -87,39 +87,53 @@ struct SegReader {
   int nseg, lane, kw;   // segments per tile, lane, values per word
   int64_t first, step;  // this warp's first tile and tile stride
   int64_t total;        // segments of all this warp's tiles
-  int64_t g0 = 0;       // global index of the current tile's segment 0
+  // issue side (counted incrementally: no divisions)
   int64_t issued = 0;   // segments issued so far
+  int64_t iss_tile = 0; // tile index (0, 1, ...) of the next segment to issue
+  int iss_seg = 0;      // and its segment within that tile
+  int iss_slot = 0;     // and its slot
+  const uint8_t* src[3] = {nullptr, nullptr, nullptr};  // this lane's three copy rows of that tile (null: past n)
+  int64_t src_tile = -1;  // the tile src[] was set for
+  // use side
+  int use_slot = 0;     // slot of the segment in hand (or of the next one)
   int cur = -1;         // segment of the current tile in hand, -1: none
   int s_end = 0;        // first sphere past the segment in hand
   const uint32_t* row = nullptr;  // this lane's row in the slot in hand
 
   __device__ __forceinline__ void issue_next() {  // warp-uniform
-    const int64_t gi = issued++;
-    if (gi < total) {
-      const int64_t kk = gi / nseg;
-      const int sg = (int)(gi - kk * nseg);
-      const int64_t r0 = (first + kk * step) * 32;
-      uint8_t* slot = slots + (gi % SEG_SLOTS) * SEG_BYTES;
-      const int64_t col = (int64_t)sg * SEG_W * 4;
+    if (issued < total) {
+      if (src_tile != iss_tile) {  // once per tile: the lane's three rows (chunk i = lane + 32 t)
+        const int64_t r0 = (first + iss_tile * step) * 32;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const int i = lane + 32 * t, r = i / 3, third = i - 3 * r;
+          src[t] = r0 + r < n ? rows + (r0 + r) * stride + 16 * third : nullptr;
+        }
+        src_tile = iss_tile;
+      }
+      const uint32_t slot = (uint32_t)__cvta_generic_to_shared(slots + iss_slot * SEG_BYTES) + 16 * lane;
+      const int col = iss_seg * SEG_W * 4;
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
-        const int i = lane + 32 * t, r = i / 3, third = i - 3 * r;
-        const int64_t off = col + 16 * third;
-        if (r0 + r < n && off < stride)  // rows past n and past the row's end stay as they are
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                           (uint32_t)__cvta_generic_to_shared(slot + 16 * i)),
-                       "l"(rows + (r0 + r) * stride + off)
+        const int third = (lane + 32 * t) % 3;
+        if (src[t] && col + 16 * third < stride)  // rows past n and past the row's end stay as they are
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(slot + 512 * t), "l"(src[t] + col)
                        : "memory");
       }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+    ++issued;
+    if (++iss_seg == nseg) {
+      iss_seg = 0;
+      ++iss_tile;
+    }
+    if (++iss_slot == SEG_SLOTS) iss_slot = 0;
   }
   __device__ __forceinline__ void start() {
     for (int i = 0; i < SEG_SLOTS; ++i) issue_next();
   }
   __device__ __forceinline__ void acquire(int c) {
-    const int64_t gs = g0 + c;
-    row = reinterpret_cast<const uint32_t*>(slots + (gs % SEG_SLOTS) * SEG_BYTES) + lane * SEG_W;
+    row = reinterpret_cast<const uint32_t*>(slots + use_slot * SEG_BYTES) + lane * SEG_W;
     s_end = 4 * kw * (c + 1);
     asm volatile("cp.async.wait_group %0;" ::"n"(SEG_SLOTS - 1) : "memory");
     __syncwarp();  // every lane's copies of this segment are visible
@@ -127,6 +141,7 @@ struct SegReader {
   __device__ __forceinline__ void release() {
     __syncwarp();  // every lane is done reading the slot
     issue_next();
+    if (++use_slot == SEG_SLOTS) use_slot = 0;
   }
   __device__ __forceinline__ void advance_to(int c) {
     while (cur < c) {
@@ -138,7 +153,6 @@ struct SegReader {
   __device__ __forceinline__ void end_tile() {
     advance_to(nseg - 1);
     release();
-    g0 += nseg;
     cur = -1;
     s_end = 0;
   }
@@ -147,7 +161,7 @@ struct SegReader {
   // shared load per value.
   template <int K>
   __device__ __forceinline__ void sphere(int s, const DevFmt& f, float& g0_, float& g1_, float& g2_) {
-    if (s >= s_end) advance_to(s / (4 * kw));
+    while (s >= s_end) advance_to(cur + 1);  // spheres come in increasing order
     const int base = 12 * kw * cur;  // first value of the segment
     float v[3];
     if constexpr (K == KIND_F32) {
@@ -213,8 +227,10 @@ __global__ void __launch_bounds__(BW_BLOCK, 4) backward_kernel(BwArgs a) {
   sr.first = first;
   sr.step = step;
   sr.total = use_ring ? my_tiles * sr.nseg : 0;
-  if (use_ring) sr.start();
   if (a.q && my_tiles > 0) q_prefetch(qbuf, a.q, first * 32, a.n, J, lane);
+  grid_dependents_may_launch();
+  grid_dependency_wait();  // the gradient rows are complete from here on
+  if (use_ring) sr.start();
 
   for (int64_t k = 0; k < my_tiles; ++k) {
     const int64_t c = (first + k * step) * 32 + lane;
@@ -268,7 +284,7 @@ static void (*bw_kernel_for(int kind))(BwArgs) {
 }
 
 cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform, Packed grad,
-                            const float* dcost, int64_t n, Packed jgrad, cudaStream_t st) {
+                            const float* dcost, int64_t n, Packed jgrad, cudaStream_t st, bool overlap) {
   BwArgs a;
   a.r = r;
   a.q = q;
@@ -290,8 +306,8 @@ cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform, Pa
   const int64_t tiles = (n + 31) / 32;
   const int64_t blocks = (tiles + BW_WARPS - 1) / BW_WARPS;
   const int64_t cap = (int64_t)sm_count() * per_sm;
-  kern<<<(int)(blocks < cap ? blocks : cap), BW_BLOCK, smem, st>>>(a);
-  return cudaGetLastError();
+  const cudaError_t e = launch_after(overlap, kern, (int)(blocks < cap ? blocks : cap), BW_BLOCK, smem, st, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace vapr

@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
   const int64_t c_end = a.slot >= 0 ? a.n : (c_begin + per_block < a.n ? c_begin + per_block : a.n);
   if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
+  grid_dependents_may_launch();  // (the next stage waits for this grid to finish)
+  grid_dependency_wait();        // the P rows are complete from here on
   auto draw = [&]() -> unsigned int {  // lane 0's ticket (the other lanes get 0)
     if (lane != 0) return 0u;
     return a.slot >= 0 ? atomicAdd(&g_sched[a.slot].next, 1u) : (unsigned int)atomicAdd(&s_next, 1);
@@ -204,7 +206,7 @@ static int sched_slot(SchedPool& P, cudaStream_t st, int64_t n, cudaEvent_t* rec
 
 cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc, const vapr_cost_params& p,
                              Packed pos, int64_t n, float* cost, Packed dist, Packed grad,
-                             cudaStream_t st, const float* est, float margin) {
+                             cudaStream_t st, const float* est, float margin, bool overlap) {
   CollArgs a;
   a.r = r;
   a.sc = sc;
@@ -235,11 +237,9 @@ cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc, const vapr
   std::lock_guard<std::mutex> hold(P.mu);  // slot choice, launch and its event together
   cudaEvent_t rec;
   a.slot = sched_slot(P, st, n, &rec);
-  if (est)
-    collision_kernel<true><<<grid, COLL_WARPS * 32, smem, st>>>(a);
-  else
-    collision_kernel<false><<<grid, COLL_WARPS * 32, smem, st>>>(a);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = est ? launch_after(overlap, collision_kernel<true>, grid, COLL_WARPS * 32, smem, st, a)
+                      : launch_after(overlap, collision_kernel<false>, grid, COLL_WARPS * 32, smem, st, a);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess && rec) return cudaEventRecord(rec, st);
   return e;
 }

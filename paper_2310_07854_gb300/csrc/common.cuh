@@ -55,13 +55,15 @@ int* tc_error_word();                   // its device address (for kernel argume
 
 cudaError_t launch_fk(const RobotArgs& r, const float* q, int64_t n, Packed pos,
                       Packed xform, cudaStream_t st);
+// overlap: launched right after the step's previous stage (vapr_cost_grad),
+// whose tail its table loading may overlap (launch_after)
 cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc,
                              const vapr_cost_params& p, Packed pos, int64_t n,
                              float* cost, Packed dist, Packed grad, cudaStream_t st,
-                             const float* est = nullptr, float margin = 0.f);
+                             const float* est = nullptr, float margin = 0.f, bool overlap = false);
 cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform,
                             Packed grad, const float* dcost, int64_t n,
-                            Packed jgrad, cudaStream_t st);
+                            Packed jgrad, cudaStream_t st, bool overlap = false);
 cudaError_t launch_fused(const RobotArgs& r, const SceneArgs& sc, const vapr_cost_params& p, const float* q,
                          const float* dcost, int64_t n, const vapr_format_table& t, float* cost, Packed dist,
                          Packed jgrad, cudaStream_t st);
@@ -69,6 +71,38 @@ cudaError_t launch_pack(const float* src, int64_t rows, int64_t row_len, Packed 
                         cudaStream_t st);
 cudaError_t launch_unpack(Packed src, int64_t rows, int64_t row_len, float* dst,
                           cudaStream_t st);
+
+// Programmatic dependent launch (the stages of a step launched back to back
+// on one stream): a kernel launched with launch_after() may start while the
+// kernel before it finishes; it must call grid_dependency_wait() before it
+// reads anything that kernel writes (until then it only loads its tables).
+// grid_dependents_may_launch() lets the next kernel start as this one's
+// blocks retire.  Both are no-ops for a kernel launched plainly.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_may_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches kern<<<grid, block, smem, st>>>(args...); with overlap, so that
+// it may start while the kernel launched before it on st finishes (it waits
+// for that kernel's results with grid_dependency_wait()).  Only the step's
+// own stages are launched this way (vapr_cost_grad): a kernel's work before
+// its wait reads only what the kernel before it does not write.
+template <typename... Params, typename... Args>
+cudaError_t launch_after(bool overlap, void (*kern)(Params...), int grid, int block, size_t smem,
+                         cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Params>(args)...);
+}
 
 // Clamps a device-table index into [lo, hi] so that a bad table can give a
 // wrong answer but never an out-of-bounds access.

@@ -21,7 +21,9 @@
 // written into its row of the warp's shared tile (rows an odd number of
 // 16-byte chunks apart: conflict-free 16-byte stores).  The tile's 32 rows
 // are one contiguous range of global memory, so the warp then copies them
-// out as whole lines, lane i taking 16-byte chunk i, i + 32, ...  (Writing
+// out as whole lines: by one bulk copy (cp.async.bulk) when the rows need
+// no padding (float32: 39 chunks), else lane i taking 16-byte chunk i,
+// i + 32, ...  (Writing
 // 48-byte pieces of 32 rows at a time, by a 2-D TMA store per segment or by
 // plain stores, was measured first: about 2.2 TB/s in float32 either way.)
 // The segments cover the padded row, so padding words are written as zero.
@@ -29,6 +31,7 @@
 // With the optional transform rows T (table->xform), each thread also keeps
 // its transforms in shared memory and writes its T row from there.
 #include "stages.cuh"
+#include "tcgen05.cuh"
 
 namespace vapr {
 
@@ -45,6 +48,7 @@ struct FkArgs {
   int tstride;  // float4 per thread of transform rows (3J rounded up to odd), 0 without T
   int nseg;     // segments per (padded) P row
   int pitch;    // bytes per row in the warp's shared tile: >= 48 nseg, an odd number of 16-byte chunks
+  int bulk;     // pitch == row stride: the tile leaves by one bulk copy (cp.async.bulk)
 };
 
 __host__ __device__ inline void carve_fk(Bump& b, const FkArgs& a, RobotSm& rb, uint8_t*& tiles,
@@ -145,6 +149,7 @@ __global__ void __launch_bounds__(FK_BLOCK) fk_kernel(FkArgs a) {
   carve_fk(b, a, rb, tiles, sQ, sT);
   load_robot(a.r, rb);
   __syncthreads();
+  grid_dependents_may_launch();  // (the next stage waits for this grid to finish)
 
   float4* myT = XF ? sT + threadIdx.x * a.tstride : nullptr;
   uint8_t* tb = tiles + (size_t)warp * 32 * a.pitch;  // this warp's 32 rows
@@ -163,6 +168,10 @@ __global__ void __launch_bounds__(FK_BLOCK) fk_kernel(FkArgs a) {
     const float* myq = qbuf + buf * 32 * J + lane * J;  // (rows past n: zeros, never stored)
     ChainWalk cw;
     cw.reset();
+    if (a.bulk) {  // the previous tile's bulk store has read the rows before they are rewritten
+      if (lane == 0) bulk_wait_read<0>();
+      __syncwarp();
+    }
     for (int g = 0; g < a.nseg; ++g) {
       if constexpr (KW <= 2) {  // all 4 KW spheres of the segment at once
         float v[12 * KW];
@@ -184,7 +193,15 @@ __global__ void __launch_bounds__(FK_BLOCK) fk_kernel(FkArgs a) {
       }
     }
     __syncwarp();
-    {  // the tile's rows are one contiguous range: lanes take its 16-byte chunks in order
+    if (a.bulk) {  // rows packed back to back, as in global memory: one bulk copy of the tile
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the rows' writes before the copy reads them
+      __syncwarp();
+      if (lane == 0) {
+        const int rows = (int)(a.n - tile * 32 < 32 ? a.n - tile * 32 : 32);
+        bulk_s2g(a.pos.ptr + tile * 32 * a.pos.stride, tb, (uint32_t)(rows * a.pos.stride));
+        bulk_commit();
+      }
+    } else {  // the tile's rows are one contiguous range: lanes take its 16-byte chunks in order
       const int rows = (int)(a.n - tile * 32 < 32 ? a.n - tile * 32 : 32);
       uint4* out = reinterpret_cast<uint4*>(a.pos.ptr + tile * 32 * a.pos.stride);
       int r = lane / cpr, ch = lane - r * cpr;  // chunk i = r cpr + ch, i = lane + 32 t
@@ -217,6 +234,7 @@ __global__ void __launch_bounds__(FK_BLOCK) fk_kernel(FkArgs a) {
     }
     __syncwarp();  // the rows are copied out and this tile's q rows read before they are reused
   }
+  if (a.bulk && lane == 0) bulk_wait<0>();
 }
 
 using FkKernel = void (*)(FkArgs);
@@ -259,6 +277,7 @@ cudaError_t launch_fk(const RobotArgs& r, const float* q, int64_t n, Packed pos,
   const int64_t words = pos.stride / 4;
   a.nseg = (int)((words + PSEG_W - 1) / PSEG_W);
   a.pitch = 16 * ((3 * a.nseg) | 1);  // odd chunk count: conflict-free 16-byte row stores
+  a.bulk = a.pitch == pos.stride;
   const FkKernel kern = xf ? fk_kernel_for<true>(pos.f) : fk_kernel_for<false>(pos.f);
   if (!kern) return cudaErrorInvalidValue;
   Bump b(nullptr);

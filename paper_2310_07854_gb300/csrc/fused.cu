@@ -11,24 +11,27 @@
 // and rounds P and G to the table's formats in registers, as storing and
 // loading them would.
 //
-// A block of FU_WARPS warps takes tiles of FU_TILE = 32 configurations.
-// Warp 0 runs their joint chains (one per lane) into a shared transform
-// tile, with the next tile's q rows already copied in (cp.async); then the
-// warps take the tile's configurations one at a time from a block counter.
-// Per configuration the warp computes its sphere centres from the tile's
-// transforms (lanes over spheres), runs the collision stage's environment
-// and self terms on them (collision_terms: the same code, so cost and D are
-// the staged path's bit for bit), writes cost and D, and runs the backward
-// pass cooperatively: lane l sums F and M over link l's spheres in index
-// order, the suffix sums over links go through the lanes in fixed order,
-// and lane j forms J_j.  (The staged backward sums in one running pass over
-// all spheres, so J agrees with it to rounding, not bit for bit.)
+// A block of FU_WARPS warps takes a contiguous range of mini-tiles of
+// FU_MT = 8 configurations, which its warps draw one at a time from a block
+// counter.  A warp runs its mini-tile's joint chains (lanes 0..7, one
+// configuration each) into its own transform rows in shared memory, then
+// takes the configurations one by one: it computes the sphere centres from
+// the transforms (lanes over spheres), runs the collision stage's
+// environment and self terms on them (collision_terms: the same code, so
+// cost and D are the staged path's bit for bit), writes cost and D, and
+// runs the backward pass cooperatively: lanes form each sphere's F = G and
+// M = c x G (G rounded to its format), lane l sums link l's in index order,
+// the suffix sums over links run from the last link down, and lane j forms
+// J_j.  (The staged backward sums in one running pass over all spheres, so
+// J agrees with it to rounding, not bit for bit.)  A first version shared
+// 32-configuration tiles across the block, behind block barriers: warps
+// idled at each tile's end, 0.61 of the staged speed at 2^20.
 #include "stages.cuh"
 
 namespace vapr {
 
 constexpr int FU_WARPS = 8;
-constexpr int FU_TILE = 32;
+constexpr int FU_MT = 8;  // configurations per mini-tile (a warp's chains)
 
 struct FusedArgs {
   RobotArgs r;
@@ -40,18 +43,20 @@ struct FusedArgs {
   DevFmt fP, fG;
   Packed dist, jgrad;
   float* cost;
-  int tstride;  // float4 per configuration in the transform tile (3J rounded up to odd)
+  int tstride;  // float4 per configuration in the transform rows (3J rounded up to odd)
+  int64_t mt_per_block;  // mini-tiles of each block's contiguous range
 };
 
 struct FusedWarp {
-  float4* C;    // [S] centres before rounding to the P format (for the backward pass)
+  float4* C;    // [S] centres before rounding to the P format; then c x G
   float4* lk;   // [2 VAPR_MAX_JOINTS] per-link sums (F, -), (M, -)
   float* jrow;  // [VAPR_MAX_JOINTS] this configuration's joint gradient
+  float4* T;    // [FU_MT][tstride] transforms of the mini-tile
 };
 
 __host__ __device__ inline void carve_fused(Bump& b, const FusedArgs& a, RobotSm& rb, SceneSm& sm,
                                             CollWarp& w_mine, FusedWarp& f_mine, int mine,
-                                            SelfScratch& scratch, float4*& sT, float*& sQ) {
+                                            SelfScratch& scratch) {
   const RobotArgs& r = a.r;
   carve_robot(b, r.J, r.S, rb);
   carve_scene(b, a.sc.O, r.NP, cluster_bound(r.S, r.J), sm);
@@ -71,8 +76,10 @@ __host__ __device__ inline void carve_fused(Bump& b, const FusedArgs& a, RobotSm
   }
   carve_self_scratch(t, r.NP, cluster_bound(r.S, r.J), scratch);  // over the warps' sets (built first)
   if (t.off > b.off) b.off = t.off;
-  sT = b.take<float4>((size_t)FU_TILE * a.tstride);
-  sQ = b.take<float>((size_t)2 * FU_TILE * r.J);
+  for (int w = 0; w < FU_WARPS; ++w) {  // (after the scratch: written once the tables are built)
+    float4* T = b.take<float4>((size_t)FU_MT * a.tstride);
+    if (w == mine) f_mine.T = T;
+  }
 }
 
 // dec(enc(x)) in format f: the value a stored and reloaded x has.
@@ -90,42 +97,35 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
   CollWarp w;
   FusedWarp fw;
   SelfScratch scratch;
-  float4* sT;
-  float* sQ;
-  carve_fused(b, a, rb, sm, w, fw, wid, scratch, sT, sQ);
+  carve_fused(b, a, rb, sm, w, fw, wid, scratch);
   load_robot(a.r, rb);
   load_scene(a.r, a.sc, a.eta, a.eta_s, sm);
   __syncthreads();
   load_clusters(J, S, rb);
   load_self(a.r, rb, sm, scratch, a.eta_s);
   init_coll_warp(a.r, w, lane);
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
   const GridHeader* grid = grid_check(a.sc, a.r, a.eta);  // null: visit every cuboid
   const uint2* cells = grid ? grid_cells(a.sc) : nullptr;
 
-  __shared__ int s_next;
-  const int64_t n_tiles = (a.n + FU_TILE - 1) / FU_TILE;
-  if (wid == 0 && blockIdx.x < n_tiles) q_prefetch(sQ, a.q, blockIdx.x * (int64_t)FU_TILE, a.n, J, lane);
-  int buf = 0;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
-    const int64_t c0 = tile * FU_TILE;
-    const int rows = (int)(a.n - c0 < FU_TILE ? a.n - c0 : FU_TILE);
-    __syncthreads();  // the previous tile's transforms are no longer read
-    if (wid == 0) {  // the tile's joint chains, the next tile's q rows in flight
-      q_wait();
-      if (tile + gridDim.x < n_tiles)
-        q_prefetch(sQ + (buf ^ 1) * FU_TILE * J, a.q, (tile + gridDim.x) * FU_TILE, a.n, J, lane);
-      fk_chain(rb, J, sQ + buf * FU_TILE * J + lane * J, sT + lane * a.tstride);
-    }
-    if (threadIdx.x == 0) s_next = 0;
-    __syncthreads();
-    for (;;) {
-      int i = 0;
-      if (lane == 0) i = atomicAdd(&s_next, 1);
-      i = __shfl_sync(FULL_MASK, i, 0);
-      if (i >= rows) break;
+  const int64_t n_mt = (a.n + FU_MT - 1) / FU_MT;
+  const int64_t mt0 = blockIdx.x * a.mt_per_block;
+  const int64_t mt1 = mt0 + a.mt_per_block < n_mt ? mt0 + a.mt_per_block : n_mt;
+  for (;;) {
+    int k = 0;
+    if (lane == 0) k = atomicAdd(&s_next, 1);
+    k = __shfl_sync(FULL_MASK, k, 0);
+    const int64_t mt = mt0 + k;
+    if (mt >= mt1) break;
+    const int64_t c0 = mt * FU_MT;
+    const int rows = (int)(a.n - c0 < FU_MT ? a.n - c0 : FU_MT);
+    if (lane < rows) fk_chain(rb, J, a.q + (c0 + lane) * J, fw.T + lane * a.tstride);
+    __syncwarp();
+    for (int i = 0; i < rows; ++i) {
       const int64_t c = c0 + i;
-      const float4* T = sT + i * a.tstride;
+      const float4* T = fw.T + i * a.tstride;
       // ---- FK: centres c_s (lanes over spheres), P rounded to its format
       for (int s = lane; s < S; s += 32) {
         const int l = rb.link0[s];
@@ -150,22 +150,27 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
       out.grad_words = 0;
       coll_cost_dist(w, S, a.dist.f, a.w_c, a.w_s * selfsum, out, lane);
       __syncwarp();
-      // ---- backward: per-link sums of F = G and M = c x G (G rounded to its format)
+      // ---- backward: per sphere F = G (rounded to its format) and M = c x G,
+      //      then per link (lane l: link l's spheres in index order)
+      for (int s = lane; s < S; s += 32) {
+        const float4 gg = w.acc[s];
+        const float g0 = round_trip(gg.y, a.fG), g1 = round_trip(gg.z, a.fG), g2 = round_trip(gg.w, a.fG);
+        const float4 cc = fw.C[s];
+        w.acc[s] = make_float4(gg.x, g0, g1, g2);
+        fw.C[s] = make_float4(cc.y * g2 - cc.z * g1, cc.z * g0 - cc.x * g2, cc.x * g1 - cc.y * g0, 0.f);
+      }
+      __syncwarp();
       if (lane < J) {
         float F0 = 0.f, F1 = 0.f, F2 = 0.f, M0 = 0.f, M1 = 0.f, M2 = 0.f;
-        for (int k = rb.start[lane]; k < rb.start[lane + 1]; ++k) {
-          const int s = rb.order[k];
-          const float4 gg = w.acc[s];
-          const float g0 = round_trip(gg.y, a.fG), g1 = round_trip(gg.z, a.fG), g2 = round_trip(gg.w, a.fG);
-          if (g0 != 0.f || g1 != 0.f || g2 != 0.f) {
-            const float4 cc = fw.C[s];
-            F0 += g0;
-            F1 += g1;
-            F2 += g2;
-            M0 += cc.y * g2 - cc.z * g1;
-            M1 += cc.z * g0 - cc.x * g2;
-            M2 += cc.x * g1 - cc.y * g0;
-          }
+        for (int k2 = rb.start[lane]; k2 < rb.start[lane + 1]; ++k2) {
+          const int s = rb.order[k2];
+          const float4 g = w.acc[s], m = fw.C[s];
+          F0 += g.y;
+          F1 += g.z;
+          F2 += g.w;
+          M0 += m.x;
+          M1 += m.y;
+          M2 += m.z;
         }
         fw.lk[2 * lane] = make_float4(F0, F1, F2, 0.f);
         fw.lk[2 * lane + 1] = make_float4(M0, M1, M2, 0.f);
@@ -227,15 +232,16 @@ cudaError_t launch_fused(const RobotArgs& r, const SceneArgs& sc, const vapr_cos
   CollWarp w;
   FusedWarp fw;
   SelfScratch scratch;
-  float4* sT;
-  float* sQ;
-  carve_fused(b, a, rb, sm, w, fw, 0, scratch, sT, sQ);
+  carve_fused(b, a, rb, sm, w, fw, 0, scratch);
   const size_t smem = b.bytes();
   const int per_sm = blocks_per_sm((const void*)fused_kernel, FU_WARPS * 32, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-  const int64_t tiles = (n + FU_TILE - 1) / FU_TILE;
+  const int64_t n_mt = (n + FU_MT - 1) / FU_MT;
   const int64_t cap = (int64_t)sm_count() * per_sm;
-  fused_kernel<<<(int)(tiles < cap ? tiles : cap), FU_WARPS * 32, smem, st>>>(a);
+  const int64_t want = (n_mt + FU_WARPS - 1) / FU_WARPS;  // at least a mini-tile per warp
+  const int grid = (int)(want < cap ? want : cap);
+  a.mt_per_block = (n_mt + grid - 1) / grid;
+  fused_kernel<<<grid, FU_WARPS * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

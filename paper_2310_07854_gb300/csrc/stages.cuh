@@ -52,6 +52,7 @@ struct RobotSm {
   int* start;     // [J+1] first slot of each link in order
   int* cl_start;  // [NC+1] cluster c = spheres order[cl_start[c] .. cl_start[c+1])
   int* cl_of;     // [S] cluster of each sphere
+  int* cl_sph;    // [NC] cluster c's spheres: s0 | s1 << 8 | s2 << 16 | count << 24
   int* n_cl;      // [1] NC
 };
 
@@ -63,6 +64,7 @@ __host__ __device__ inline void carve_robot(Bump& b, int J, int S, RobotSm& r) {
   r.start = b.take<int>(J + 1);
   r.cl_start = b.take<int>(cluster_bound(S, J) + 1);
   r.cl_of = b.take<int>(S);
+  r.cl_sph = b.take<int>(cluster_bound(S, J));
   r.n_cl = b.take<int>(1);
 }
 
@@ -118,6 +120,13 @@ __device__ inline void load_clusters(int J, int S, const RobotSm& r) {
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
     const int s = r.order[k], j = r.link0[s];
     r.cl_of[s] = clusters_before(j) + (k - r.start[j]) / CL;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < r.n_cl[0]; c += blockDim.x) {
+    const int k0 = r.cl_start[c], k1 = r.cl_start[c + 1];
+    int packed = (k1 - k0) << 24;
+    for (int k = k0; k < k1; ++k) packed |= r.order[k] << (8 * (k - k0));
+    r.cl_sph[c] = packed;
   }
   __syncthreads();
 }
@@ -559,25 +568,31 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
                                             int S, float w_s, int lane) {
   const int NC = rb.n_cl[0], NG = m.self_meta[0];
   const float eta_s = __int_as_float(m.self_meta[1]);
+  static_assert(CL == 3, "a cluster's spheres are packed three to a word");
   for (int c = lane; c < NC; c += 32) {
-    const int k0 = rb.cl_start[c], k1 = rb.cl_start[c + 1];
+    const int packed = rb.cl_sph[c], cnt = packed >> 24;
+    float4 p[CL];
+#pragma unroll
+    for (int k = 0; k < CL; ++k) p[k] = w.P[k < cnt ? (packed >> (8 * k)) & 0xff : packed & 0xff];
     float sx = 0.f, sy = 0.f, sz = 0.f;
-    for (int k = k0; k < k1; ++k) {
-      const float4 p = w.P[rb.order[k]];
-      sx += p.x;
-      sy += p.y;
-      sz += p.z;
-    }
-    const float inv = __fdividef(1.f, (float)(k1 - k0));
+#pragma unroll
+    for (int k = 0; k < CL; ++k)
+      if (k < cnt) {
+        sx += p[k].x;
+        sy += p[k].y;
+        sz += p[k].z;
+      }
+    const float inv = __fdividef(1.f, (float)cnt);
     const float cx = sx * inv, cy = sy * inv, cz = sz * inv;
     float rho = 0.f;
-    for (int k = k0; k < k1; ++k) {
-      const float4 p = w.P[rb.order[k]];
-      const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
-      const float e2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      // |c_s - centroid| from the hardware reciprocal square root, rounded up
-      rho = fmaxf(rho, fmaf(e2 > 0.f ? e2 * rsqrtf(e2) : 0.f, 1.000001f, p.w));
-    }
+#pragma unroll
+    for (int k = 0; k < CL; ++k)
+      if (k < cnt) {
+        const float dx = p[k].x - cx, dy = p[k].y - cy, dz = p[k].z - cz;
+        const float e2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        // |c_s - centroid| from the hardware reciprocal square root, rounded up
+        rho = fmaxf(rho, fmaf(e2 > 0.f ? e2 * rsqrtf(e2) : 0.f, 1.000001f, p[k].w));
+      }
     w.cls[c] = make_float4(cx, cy, cz, rho);
   }
   __syncwarp();
@@ -629,7 +644,10 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
       }
       // active pairs in table order (lane order within the chunk), one at a
       // time: the pair's own lane updates both spheres' gradients, so every
-      // sphere receives its self terms in that order
+      // sphere receives its self terms in that order.  (Updating all at once
+      // when no two active pairs of a chunk share a sphere was measured and
+      // is slower, as is listing the kept cluster pairs of all chunks first
+      // and expanding them together.)
       unsigned am = __ballot_sync(FULL_MASK, act);
       if (act) selfsum += pen;
       while (am) {

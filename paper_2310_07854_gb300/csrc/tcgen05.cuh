@@ -66,6 +66,13 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
                "r"(x), "r"(y), "r"(sm_addr(src))
                : "memory");
 }
+// 1-D bulk copy of `bytes` (a multiple of 16) from shared to global memory
+// (both 16-byte aligned), tracked in the issuing thread's bulk groups.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(sm_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Until at most N of this thread's committed bulk groups still read shared memory.
 template <int N>
