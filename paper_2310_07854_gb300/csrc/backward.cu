@@ -10,8 +10,11 @@
 //       = (a_j . M - b_j . F) - (a_j . M_{<j} - b_j . F_{<j}),
 // so one pass over the links in chain order suffices: when joint j is
 // reached the thread records a_j, b_j and K_j = a_j . M_{<j} - b_j . F_{<j},
-// and the totals finish every J_j at the end.  Zero gradients are skipped
-// (the sparsity of Sec. III-C).
+// and the totals finish every J_j at the end.  A link's spheres enter
+// through sums in the link's frame, f = sum G_s and W = sum G_s p_s^T, and
+// its moment sum c_s x G_s = t x f + (antisymmetric part of R W^T) costs a
+// few multiply-adds per link (LinkSums in stages.cuh): 12 multiply-adds
+// per sphere.
 //
 // One thread per configuration; a warp owns tiles of 32 consecutive
 // configurations, whose gradient rows are contiguous in global memory.  The
@@ -232,12 +235,18 @@ __global__ void __launch_bounds__(BW_BLOCK, 4) backward_kernel(BwArgs a) {
   grid_dependency_wait();  // the gradient rows are complete from here on
   if (use_ring) sr.start();
 
+  // Between two tiles' q copies each lane commits one ring group per
+  // segment (nseg of them, the ring's start() the first time), so the q rows
+  // of a tile have landed once at most min(nseg, SEG_SLOTS) groups are
+  // pending: the ring's copies stay in flight across the wait.
+  static_assert(SEG_SLOTS <= 3, "q_wait_after takes at most 3 groups in flight");
+  const int q_after = use_ring ? (sr.nseg < SEG_SLOTS ? sr.nseg : SEG_SLOTS) : 0;
   for (int64_t k = 0; k < my_tiles; ++k) {
     const int64_t c = (first + k * step) * 32 + lane;
     const bool live = c < a.n;
     const float* qp = nullptr;
     if (a.q) {  // this tile's q rows, and the next tile's in flight
-      q_wait();
+      q_wait_after(q_after);
       if (k + 1 < my_tiles) q_prefetch(qbuf + ((k + 1) & 1) * 32 * J, a.q, (first + (k + 1) * step) * 32, a.n, J, lane);
       qp = qbuf + (k & 1) * 32 * J + lane * J;
     }

@@ -7,7 +7,8 @@
 //   FK         T_j = T_{j-1} F_j Rz(q_j), c_s = T_link(s) [p_s; 1]
 //   collision  C = w_c sum_s D_s + w_s sum P_ij, G = dC/dc
 //   backward   J_j = dC (a_j . M_{>=j} - b_j . F_{>=j}), F = sum G_s,
-//              M = sum c_s x G_s over the spheres on links >= j
+//              M = sum c_s x G_s over the spheres on links >= j (from
+//              per-link sums in the link's frame, LinkSums)
 // and rounds P and G to the table's formats in registers, as storing and
 // loading them would.
 //
@@ -19,11 +20,12 @@
 // the transforms (lanes over spheres), runs the collision stage's
 // environment and self terms on them (collision_terms: the same code, so
 // cost and D are the staged path's bit for bit), writes cost and D, and
-// runs the backward pass cooperatively: lanes form each sphere's F = G and
-// M = c x G (G rounded to its format), lane l sums link l's in index order,
-// the suffix sums over links run from the last link down, and lane j forms
-// J_j.  (The staged backward sums in one running pass over all spheres, so
-// J agrees with it to rounding, not bit for bit.)  A first version shared
+// runs the backward pass cooperatively: lanes round G to its format, lane l
+// forms link l's sums and moment (LinkSums, spheres in the robot's order),
+// and lane j runs the staged backward's running totals over the links to
+// form K_j and J_j.  Every sum is taken in the staged pass's order with the
+// same operations, so J is the staged path's bit for bit too (with the
+// transforms recomputed there, not stored).  A first version shared
 // 32-configuration tiles across the block, behind block barriers: warps
 // idled at each tile's end, 0.61 of the staged speed at 2^20.
 #include "stages.cuh"
@@ -48,7 +50,6 @@ struct FusedArgs {
 };
 
 struct FusedWarp {
-  float4* C;    // [S] centres before rounding to the P format; then c x G
   float4* lk;   // [2 VAPR_MAX_JOINTS] per-link sums (F, -), (M, -)
   float* jrow;  // [VAPR_MAX_JOINTS] this configuration's joint gradient
   float4* T;    // [FU_MT][tstride] transforms of the mini-tile
@@ -66,7 +67,6 @@ __host__ __device__ inline void carve_fused(Bump& b, const FusedArgs& a, RobotSm
     CollWarp cw;
     carve_coll_warp(b, r.S, r.J, cw);
     FusedWarp fw;
-    fw.C = b.take<float4>(r.S);
     fw.lk = b.take<float4>(2 * VAPR_MAX_JOINTS);
     fw.jrow = b.take<float>(VAPR_MAX_JOINTS);
     if (w == mine) {
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
     for (int i = 0; i < rows; ++i) {
       const int64_t c = c0 + i;
       const float4* T = fw.T + i * a.tstride;
-      // ---- FK: centres c_s (lanes over spheres), P rounded to its format
+      // ---- FK: centres c_s (lanes over spheres), rounded to the P format
       for (int s = lane; s < S; s += 32) {
         const int l = rb.link0[s];
         const float4 r0 = T[3 * l], r1 = T[3 * l + 1], r2 = T[3 * l + 2];
@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
         const float cx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
         const float cy = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
         const float cz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
-        fw.C[s] = make_float4(cx, cy, cz, 0.f);
         const float4 old = w.P[s];  // .w: the radius
         w.P[s] = make_float4(round_trip(cx, a.fP), round_trip(cy, a.fP), round_trip(cz, a.fP), old.w);
       }
@@ -150,51 +149,56 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
       out.grad_words = 0;
       coll_cost_dist(w, S, a.dist.f, a.w_c, a.w_s * selfsum, out, lane);
       __syncwarp();
-      // ---- backward: per sphere F = G (rounded to its format) and M = c x G,
-      //      then per link (lane l: link l's spheres in index order)
-      for (int s = lane; s < S; s += 32) {
-        const float4 gg = w.acc[s];
-        const float g0 = round_trip(gg.y, a.fG), g1 = round_trip(gg.z, a.fG), g2 = round_trip(gg.w, a.fG);
-        const float4 cc = fw.C[s];
-        w.acc[s] = make_float4(gg.x, g0, g1, g2);
-        fw.C[s] = make_float4(cc.y * g2 - cc.z * g1, cc.z * g0 - cc.x * g2, cc.x * g1 - cc.y * g0, 0.f);
+      // ---- backward: G rounded to its format (lanes over spheres), then
+      //      lane l forms link l's sums and moment, and lane j runs the
+      //      staged pass's running totals over the links to form J_j
+      if (a.fG.kind != KIND_F32) {
+        for (int s = lane; s < S; s += 32) {
+          const float4 gg = w.acc[s];
+          w.acc[s] = make_float4(gg.x, round_trip(gg.y, a.fG), round_trip(gg.z, a.fG), round_trip(gg.w, a.fG));
+        }
+        __syncwarp();
+      }
+      float R[3][3], t[3];
+      if (lane < J) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float4 rk = T[3 * lane + k];
+          R[k][0] = rk.x;
+          R[k][1] = rk.y;
+          R[k][2] = rk.z;
+          t[k] = rk.w;
+        }
+        LinkSums ls;
+        ls.zero();
+        for (int k2 = rb.start[lane]; k2 < rb.start[lane + 1]; ++k2) {
+          const int s = rb.order[k2];
+          const float4 g = w.acc[s];
+          ls.add(g.y, g.z, g.w, rb.sph[s]);
+        }
+        float mo[3];
+        ls.moment(R, t, mo);
+        fw.lk[2 * lane] = make_float4(ls.f[0], ls.f[1], ls.f[2], 0.f);
+        fw.lk[2 * lane + 1] = make_float4(mo[0], mo[1], mo[2], 0.f);
       }
       __syncwarp();
       if (lane < J) {
-        float F0 = 0.f, F1 = 0.f, F2 = 0.f, M0 = 0.f, M1 = 0.f, M2 = 0.f;
-        for (int k2 = rb.start[lane]; k2 < rb.start[lane + 1]; ++k2) {
-          const int s = rb.order[k2];
-          const float4 g = w.acc[s], m = fw.C[s];
-          F0 += g.y;
-          F1 += g.z;
-          F2 += g.w;
-          M0 += m.x;
-          M1 += m.y;
-          M2 += m.z;
-        }
-        fw.lk[2 * lane] = make_float4(F0, F1, F2, 0.f);
-        fw.lk[2 * lane + 1] = make_float4(M0, M1, M2, 0.f);
-      }
-      __syncwarp();
-      if (lane < J) {  // suffix sums from the last link down, then J_j
-        float F0 = 0.f, F1 = 0.f, F2 = 0.f, M0 = 0.f, M1 = 0.f, M2 = 0.f;
-        for (int l = J - 1; l >= lane; --l) {
+        float ax, ay, az, bx, by, bz;
+        joint_axis(R, t, ax, ay, az, bx, by, bz);
+        float M[3] = {0.f, 0.f, 0.f}, F[3] = {0.f, 0.f, 0.f};
+        float K = 0.f;
+        for (int l = 0; l < J; ++l) {
+          if (l == lane) K = axis_term(ax, ay, az, bx, by, bz, M, F);
           const float4 f = fw.lk[2 * l], m = fw.lk[2 * l + 1];
-          F0 += f.x;
-          F1 += f.y;
-          F2 += f.z;
-          M0 += m.x;
-          M1 += m.y;
-          M2 += m.z;
+          M[0] = __fadd_rn(M[0], m.x);
+          M[1] = __fadd_rn(M[1], m.y);
+          M[2] = __fadd_rn(M[2], m.z);
+          F[0] = __fadd_rn(F[0], f.x);
+          F[1] = __fadd_rn(F[1], f.y);
+          F[2] = __fadd_rn(F[2], f.z);
         }
-        const int j = lane;
-        const float4 r0 = T[3 * j], r1 = T[3 * j + 1], r2 = T[3 * j + 2];
-        const float ax = r0.z, ay = r1.z, az = r2.z;  // axis a_j: z-column of T_j
-        const float bx = ay * r2.w - az * r1.w;       // b_j = a_j x o_j
-        const float by = az * r0.w - ax * r2.w;
-        const float bz = ax * r1.w - ay * r0.w;
         const float dc = a.dcost ? a.dcost[c] : 1.f;
-        fw.jrow[j] = dc * ((ax * M0 + ay * M1 + az * M2) - (bx * F0 + by * F1 + bz * F2));
+        fw.jrow[lane] = __fmul_rn(dc, __fsub_rn(axis_term(ax, ay, az, bx, by, bz, M, F), K));
       }
       __syncwarp();
       {

@@ -133,6 +133,20 @@ __device__ inline void load_clusters(int J, int S, const RobotSm& r) {
 
 // ------------------------------------------------------------ FK (thread)
 // One step of the joint chain: (R, t) = T_{j-1} becomes T_j = T_{j-1} F_j Rz(q_j).
+// sin and cos of a joint angle: q reduced to [-pi, pi] as r = q - 2 pi k,
+// k the integer nearest q / 2 pi (Cody-Waite reduction: 2 pi split into its
+// float and the float of the remainder, each subtracted by one fused
+// multiply-add; r = q exactly for |q| <= pi, and r is off by far less than
+// the approximation error below for |q| up to thousands of radians), then
+// the hardware approximations, whose absolute error on [-pi, pi] is at most
+// 2^-21.4 (about 4e-7, under the float32 tolerance of the whole path).
+__device__ __forceinline__ void joint_sincos(float q, float& sn, float& cs) {
+  const float k = rintf(q * 0.159154943f);  // 1 / (2 pi)
+  float r = fmaf(-k, 6.28318548f, q);       // float(2 pi) = 2 pi + 1.7484555e-7
+  r = fmaf(k, 1.74845553e-7f, r);
+  __sincosf(r, &sn, &cs);
+}
+
 __device__ __forceinline__ void joint_step(const RobotSm& r, int j, float qj, float (&R)[3][3], float (&t)[3]) {
   const float4 f0 = r.F[3 * j], f1 = r.F[3 * j + 1], f2 = r.F[3 * j + 2];
   float B[3][3], tb[3];
@@ -144,7 +158,7 @@ __device__ __forceinline__ void joint_step(const RobotSm& r, int j, float qj, fl
     tb[k] = fmaf(R[k][0], f0.w, fmaf(R[k][1], f1.w, fmaf(R[k][2], f2.w, t[k])));
   }
   float sn, cs;
-  sincosf(qj, &sn, &cs);
+  joint_sincos(qj, sn, cs);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {  // ... Rz(q_j)
     R[k][0] = fmaf(cs, B[k][0], sn * B[k][1]);
@@ -182,6 +196,17 @@ __device__ __forceinline__ void q_prefetch(float* dst, const float* q, int64_t c
 }
 __device__ __forceinline__ void q_wait() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+}
+// The same when `after` (0..3) later commit groups of this thread may stay
+// in flight (copies issued after the q rows).
+__device__ __forceinline__ void q_wait_after(int after) {
+  switch (after) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+  }
   __syncwarp();
 }
 
@@ -837,9 +862,73 @@ struct RowReader {
   }
 };
 
+// Backward pass building blocks, shared by every kernel that forms the
+// joint gradient so that they all round alike.  Link l's spheres enter
+// through sums in the link's own frame,
+//   f = sum_s G_s,   W = sum_s G_s p_s^T   (p_s the sphere's offset on the link),
+// which need no pose; with the link's pose (R, t), c_s = R p_s + t gives
+//   sum_s c_s x G_s = t x f + sum_s (R p_s) x G_s,
+// and (R p_s) x G_s summed over s is the antisymmetric part of U = R W^T
+// (U_km = sum_l R_kl W_ml = sum_s (R p_s)_k G_s,m):
+//   (U_12 - U_21, U_20 - U_02, U_01 - U_10).
+// 12 multiply-adds per sphere instead of 21 for forming c_s and c_s x G_s.
+struct LinkSums {
+  float f[3], W[3][3];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      f[m] = 0.f;
+#pragma unroll
+      for (int l = 0; l < 3; ++l) W[m][l] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void add(float g0, float g1, float g2, const float4& p) {
+    const float g[3] = {g0, g1, g2};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      f[m] = __fadd_rn(f[m], g[m]);
+      W[m][0] = fmaf(g[m], p.x, W[m][0]);
+      W[m][1] = fmaf(g[m], p.y, W[m][1]);
+      W[m][2] = fmaf(g[m], p.z, W[m][2]);
+    }
+  }
+  // sum_s c_s x G_s for the link at pose (R, t)
+  __device__ __forceinline__ void moment(const float (&R)[3][3], const float (&t)[3], float (&mo)[3]) const {
+    float U[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) U[k][m] = fmaf(R[k][0], W[m][0], fmaf(R[k][1], W[m][1], __fmul_rn(R[k][2], W[m][2])));
+    mo[0] = __fadd_rn(fmaf(t[1], f[2], -__fmul_rn(t[2], f[1])), __fsub_rn(U[1][2], U[2][1]));
+    mo[1] = __fadd_rn(fmaf(t[2], f[0], -__fmul_rn(t[0], f[2])), __fsub_rn(U[2][0], U[0][2]));
+    mo[2] = __fadd_rn(fmaf(t[0], f[1], -__fmul_rn(t[1], f[0])), __fsub_rn(U[0][1], U[1][0]));
+  }
+};
+
+// a . M - b . F
+__device__ __forceinline__ float axis_term(float ax, float ay, float az, float bx, float by, float bz,
+                                           const float (&M)[3], const float (&F)[3]) {
+  return __fsub_rn(fmaf(ax, M[0], fmaf(ay, M[1], __fmul_rn(az, M[2]))),
+                   fmaf(bx, F[0], fmaf(by, F[1], __fmul_rn(bz, F[2]))));
+}
+
+// The axis a_j (z-column of R_j) and b_j = a_j x o_j (o_j = t_j) of joint j.
+__device__ __forceinline__ void joint_axis(const float (&R)[3][3], const float (&t)[3], float& ax, float& ay,
+                                           float& az, float& bx, float& by, float& bz) {
+  ax = R[0][2];
+  ay = R[1][2];
+  az = R[2][2];
+  bx = fmaf(ay, t[2], -__fmul_rn(az, t[1]));
+  by = fmaf(az, t[0], -__fmul_rn(ax, t[2]));
+  bz = fmaf(ax, t[1], -__fmul_rn(ay, t[0]));
+}
+
 // Joint gradient of one configuration: put(j, dc * J_j) for j < J, with the
 // per-joint terms (a_j, K_j), (b_j, -) in myK[0], myK[kst], .. myK[(2J-1) kst].
-// live == false runs the same control flow without touching memory.
+// One pass over the links in chain order: at joint j the running totals
+// M, F hold links < j, so K_j = a_j . M - b_j . F, and at the end
+// J_j = (a_j . M - b_j . F) - K_j over all links (= links >= j).
+// live == false runs the same control flow (its results are not stored).
 // The gradient reader g gives the three values of a sphere (g.sphere); all
 // lanes of a warp ask for the same sphere at the same time (the sphere
 // order is the robot's, shared by all lanes).
@@ -849,7 +938,7 @@ __device__ __forceinline__ void backward_config(const RobotSm& rb, int J, bool l
                                                 float4* myK, int kst, Put put) {
   float R[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
   float t[3] = {0.f, 0.f, 0.f};
-  float F0 = 0.f, F1 = 0.f, F2 = 0.f, M0 = 0.f, M1 = 0.f, M2 = 0.f;
+  float F[3] = {0.f, 0.f, 0.f}, M[3] = {0.f, 0.f, 0.f};
   for (int j = 0; j < J; ++j) {
     if (live) {
       if (x.row) {  // stored transforms: element e of T_j is value 12j + e
@@ -863,37 +952,29 @@ __device__ __forceinline__ void backward_config(const RobotSm& rb, int J, bool l
         joint_step(rb, j, q[j], R, t);
       }
     }
-    // axis a_j, b_j = a_j x o_j, and the correction K_j
-    const float ax = R[0][2], ay = R[1][2], az = R[2][2];
-    const float bx = ay * t[2] - az * t[1];
-    const float by = az * t[0] - ax * t[2];
-    const float bz = ax * t[1] - ay * t[0];
-    const float K = (ax * M0 + ay * M1 + az * M2) - (bx * F0 + by * F1 + bz * F2);
-    myK[2 * j * kst] = make_float4(ax, ay, az, K);
+    float ax, ay, az, bx, by, bz;
+    joint_axis(R, t, ax, ay, az, bx, by, bz);
+    myK[2 * j * kst] = make_float4(ax, ay, az, axis_term(ax, ay, az, bx, by, bz, M, F));
     myK[(2 * j + 1) * kst] = make_float4(bx, by, bz, 0.f);
-    // spheres on link j: F += G, M += c x G (zero gradients add nothing)
+    LinkSums ls;
+    ls.zero();
     for (int idx = rb.start[j]; idx < rb.start[j + 1]; ++idx) {
       const int s = rb.order[idx];
       float g0, g1, g2;
       g.template sphere<GK>(s, fg, g0, g1, g2);
-      if (live && (g0 != 0.f || g1 != 0.f || g2 != 0.f)) {
-        const float4 p = rb.sph[s];
-        const float c0 = fmaf(R[0][0], p.x, fmaf(R[0][1], p.y, fmaf(R[0][2], p.z, t[0])));
-        const float c1 = fmaf(R[1][0], p.x, fmaf(R[1][1], p.y, fmaf(R[1][2], p.z, t[1])));
-        const float c2 = fmaf(R[2][0], p.x, fmaf(R[2][1], p.y, fmaf(R[2][2], p.z, t[2])));
-        F0 += g0;
-        F1 += g1;
-        F2 += g2;
-        M0 += c1 * g2 - c2 * g1;
-        M1 += c2 * g0 - c0 * g2;
-        M2 += c0 * g1 - c1 * g0;
-      }
+      ls.add(g0, g1, g2, rb.sph[s]);
+    }
+    float mo[3];
+    ls.moment(R, t, mo);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      M[k] = __fadd_rn(M[k], mo[k]);
+      F[k] = __fadd_rn(F[k], ls.f[k]);
     }
   }
   for (int j = 0; j < J; ++j) {
     const float4 ak = myK[2 * j * kst], b = myK[(2 * j + 1) * kst];
-    const float Jj = (ak.x * M0 + ak.y * M1 + ak.z * M2) - (b.x * F0 + b.y * F1 + b.z * F2) - ak.w;
-    put(j, dc * Jj);
+    put(j, __fmul_rn(dc, __fsub_rn(axis_term(ak.x, ak.y, ak.z, b.x, b.y, b.z, M, F), ak.w)));
   }
 }
 

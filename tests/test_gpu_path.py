@@ -36,6 +36,29 @@ def test_fk_fp32(wl):
     check_fp32(decode_packed(xf, 12 * J, F.FP32), wl["xf64"].reshape(w.n, -1), what="T")
 
 
+def test_fk_large_angles():
+    """Joint angles far outside [-pi, pi] (the kernels reduce an angle by
+    multiples of 2 pi before taking its sine and cosine), at +-pi and at
+    multiples of 2 pi, against the FP64 oracle; the backward pass recomputes
+    the same chain, so its joint gradient is checked on the same angles."""
+    w = synth.make_workload("sweep_1024")
+    J, S, n = w.robot.n_joints, w.robot.n_spheres, 256
+    rng = np.random.default_rng(41)
+    q = rng.uniform(-300.0, 300.0, size=(n, J)).astype(np.float32)
+    q[:16] = np.float32(np.pi) * rng.choice([-1.0, 1.0], size=(16, J)).astype(np.float32)
+    q[16:32] = (2.0 * np.pi * rng.integers(-40, 40, size=(16, J))).astype(np.float32)
+    q[32:48] = np.nextafter(q[:16], np.float32(0.0))  # just inside +-pi
+    gp = GpuPath(w.robot, w.scene, w.params)
+    pos, xf = gp.fk(to_dev(q), n, F.FP32_TABLE, with_xform=True)
+    pos64, xf64 = oracle.fk(w.robot, q, with_xform=True)
+    check_fp32(decode_packed(pos, 3 * S, F.FP32), pos64.reshape(n, -1), what="P")
+    check_fp32(decode_packed(xf, 12 * J, F.FP32), xf64.reshape(n, -1), what="T")
+    g = synth.make_dcost(5, n * 3 * S).reshape(n, S, 3) - 1.0  # any sphere gradient
+    g_dev, g32 = oracle_packed(g.reshape(n, -1), F.FP32)
+    jg = gp.backward(to_dev(q), None, g_dev, None, n, F.FP32_TABLE)
+    check_fp32(decode_packed(jg, J, F.FP32), oracle.backward(w.robot, q, g32.reshape(n, S, 3)), what="J")
+
+
 @pytest.mark.parametrize("fmt", [F.BF16, F.FP16, F.E4M3, F.E5M2, F.E3M2, F.E2M1, F.fmt(3, 1),
                                  F.fmt(2, 2), F.fmt(6, 6), F.fmt(4, 5)], ids=str)
 def test_fk_reduced(wl, fmt):
