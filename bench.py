@@ -768,7 +768,8 @@ def surrogate_leg(w, ev32, q, n, args, flush, torch, peaks, peak_kind, light=Fal
 
 def kernel_mode(args):
     """One stage alone, for ncu captures: a fixed number of launches of one
-    kernel on a chosen size, no flush, no other legs."""
+    kernel on a chosen size (timed as one CUDA graph), no flush, no other
+    legs."""
     import torch
     from paper_2310_07854_gb300 import binding as B
     from paper_2310_07854_gb300.path import Evaluator
@@ -801,10 +802,17 @@ def kernel_mode(args):
     for _ in range(args.warmup):
         fn()
     torch.cuda.synchronize()
+    # the launches as one CUDA graph, so that host-side launch costs do not
+    # show in the device time of small launches
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(args.steps):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
-        fn()
+    g.replay()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps

@@ -67,6 +67,8 @@ DevFmt make_dev_fmt(vapr_format fm) {
   const unsigned fl = fm.flags;
   f.fastdec = f.E < 8 && !f.ieee && !f.fn;
   f.dec_scale = std::ldexp(1.0f, 127 - f.bias);
+  f.enc_scale = std::ldexp(1.0f, f.bias - 127);
+  f.enc_lo = (uint32_t)(127 + f.emin) << 23;
   f.kind = KIND_GENERIC;
   if (f.E == 5 && f.M == 10 && fl == VAPR_FMT_IEEE) f.kind = KIND_F16;
   if (f.E == 8 && f.M == 7 && fl == VAPR_FMT_IEEE) f.kind = KIND_BF16;

@@ -74,63 +74,79 @@ __host__ __device__ inline void carve_bw(Bump& b, const BwArgs& a, RobotSm& rb, 
 // lane holds the same copy of the bookkeeping (all calls are warp-uniform).
 // A segment holds 12k values (k per word) of each row, i.e. spheres
 // 4k c .. 4k c + 4k - 1 of segment c, so a sphere's three values never
-// straddle two segments; the spheres must come in increasing index order.
+// straddle two segments; segments are used in increasing order.
 //
 // A segment of the warp's 32 rows is 96 chunks of 16 bytes; lane m copies
 // chunks m, m + 32 and m + 64 (chunk i: row i / 3, third i % 3 of the
 // segment row) with cp.async, so each copy instruction reads whole runs of
-// about 11 consecutive rows and the slot fills linearly.  Every segment is
-// one commit group of each lane, and every release commits one group (empty
-// past the last segment), so waiting until at most SEG_SLOTS - 1 groups are
-// pending always means the segment in hand has landed.
+// about 11 consecutive rows and the slot fills linearly.  The lane's three
+// chunks sit at fixed offsets from the tile's first row, so a copy costs an
+// add and two compares.  Every segment is one commit group of each lane,
+// and every release commits one group (empty past the last segment), so
+// waiting until at most SEG_SLOTS - 1 groups are pending always means the
+// segment in hand has landed.
 struct SegReader {
   uint8_t* slots;       // this warp's [SEG_SLOTS][32 rows][SEG_W words]
-  const uint8_t* rows;  // the gradient rows
-  int64_t stride, n;    // row stride (bytes), rows
-  int nseg, lane, kw;   // segments per tile, lane, values per word
-  int64_t first, step;  // this warp's first tile and tile stride
-  int64_t total;        // segments of all this warp's tiles
-  // issue side (counted incrementally: no divisions)
-  int64_t issued = 0;   // segments issued so far
-  int64_t iss_tile = 0; // tile index (0, 1, ...) of the next segment to issue
-  int iss_seg = 0;      // and its segment within that tile
-  int iss_slot = 0;     // and its slot
-  const uint8_t* src[3] = {nullptr, nullptr, nullptr};  // this lane's three copy rows of that tile (null: past n)
-  int64_t src_tile = -1;  // the tile src[] was set for
+  int nseg, kw;         // segments per tile, values per word
+  // issue side
+  int off[3], lim[3], rt[3];  // this lane's chunks: offset from the tile's first row, end of
+                              // the row's bytes (copy while col < lim), row in the tile
+  const uint8_t* tile = nullptr;  // first row of the tile being issued
+  int64_t row0 = 0, row_step = 0, n = 0;  // its first row, rows between this warp's tiles, rows
+  int64_t tile_step = 0;  // bytes between this warp's tiles
+  int tile_rows = 0;    // rows of the tile being issued below n (clamped to 32)
+  int col = 0;          // byte offset in the rows of the next segment to issue
+  int seg_bytes = 0;    // bytes of the rows that one tile's segments cover
+  int left = 0;         // segments still to issue
+  int iss_slot = 0;     // slot of the next segment to issue
   // use side
   int use_slot = 0;     // slot of the segment in hand (or of the next one)
   int cur = -1;         // segment of the current tile in hand, -1: none
   int s_end = 0;        // first sphere past the segment in hand
   const uint32_t* row = nullptr;  // this lane's row in the slot in hand
+  int lane;
 
+  __device__ __forceinline__ void init(uint8_t* sl, const uint8_t* rows, int64_t stride, int64_t n_, int S, int k,
+                                       int ln, int64_t first, int64_t step, int64_t tiles) {
+    slots = sl;
+    kw = k;
+    lane = ln;
+    nseg = (3 * S + 12 * k - 1) / (12 * k);
+    seg_bytes = nseg * SEG_W * 4;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int i = ln + 32 * t, r = i / 3, third = i - 3 * r;
+      off[t] = (int)(r * stride) + 16 * third;
+      lim[t] = (int)stride - 16 * third;
+      rt[t] = r;
+    }
+    n = n_;
+    row0 = first * 32;
+    row_step = step * 32;
+    tile = rows + row0 * stride;
+    tile_step = row_step * stride;
+    tile_rows = (int)(n - row0 < 32 ? (n - row0 > 0 ? n - row0 : 0) : 32);
+    left = (int)(tiles * nseg);
+  }
   __device__ __forceinline__ void issue_next() {  // warp-uniform
-    if (issued < total) {
-      if (src_tile != iss_tile) {  // once per tile: the lane's three rows (chunk i = lane + 32 t)
-        const int64_t r0 = (first + iss_tile * step) * 32;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const int i = lane + 32 * t, r = i / 3, third = i - 3 * r;
-          src[t] = r0 + r < n ? rows + (r0 + r) * stride + 16 * third : nullptr;
-        }
-        src_tile = iss_tile;
-      }
+    if (left > 0) {
       const uint32_t slot = (uint32_t)__cvta_generic_to_shared(slots + iss_slot * SEG_BYTES) + 16 * lane;
-      const int col = iss_seg * SEG_W * 4;
 #pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int third = (lane + 32 * t) % 3;
-        if (src[t] && col + 16 * third < stride)  // rows past n and past the row's end stay as they are
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(slot + 512 * t), "l"(src[t] + col)
+      for (int t = 0; t < 3; ++t)
+        if (rt[t] < tile_rows && col < lim[t])  // rows past n and past the row's end stay as they are
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(slot + 512 * t), "l"(tile + off[t] + col)
                        : "memory");
+      --left;
+      col += SEG_W * 4;
+      if (col == seg_bytes) {  // next tile
+        col = 0;
+        row0 += row_step;
+        tile += tile_step;
+        tile_rows = (int)(n - row0 < 32 ? (n - row0 > 0 ? n - row0 : 0) : 32);
       }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    ++issued;
-    if (++iss_seg == nseg) {
-      iss_seg = 0;
-      ++iss_tile;
-    }
-    if (++iss_slot == SEG_SLOTS) iss_slot = 0;
+    iss_slot = iss_slot == SEG_SLOTS - 1 ? 0 : iss_slot + 1;
   }
   __device__ __forceinline__ void start() {
     for (int i = 0; i < SEG_SLOTS; ++i) issue_next();
@@ -144,7 +160,7 @@ struct SegReader {
   __device__ __forceinline__ void release() {
     __syncwarp();  // every lane is done reading the slot
     issue_next();
-    if (++use_slot == SEG_SLOTS) use_slot = 0;
+    use_slot = use_slot == SEG_SLOTS - 1 ? 0 : use_slot + 1;
   }
   __device__ __forceinline__ void advance_to(int c) {
     while (cur < c) {
@@ -160,8 +176,34 @@ struct SegReader {
     s_end = 0;
   }
   __device__ __forceinline__ void finish() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+  // Words wi WW .. wi WW + WW - 1 of this lane's row in the segment in hand
+  // (16-, 8- or 4-byte shared loads: a row is 48 bytes, 16-byte aligned).
+  template <int WW>
+  __device__ __forceinline__ void window(int wi, uint32_t (&wd)[WW]) const {
+    const uint32_t* p = row + wi * WW;
+    if constexpr (WW % 4 == 0) {
+#pragma unroll
+      for (int v = 0; v < WW / 4; ++v) {
+        const uint4 x = reinterpret_cast<const uint4*>(p)[v];
+        wd[4 * v] = x.x;
+        wd[4 * v + 1] = x.y;
+        wd[4 * v + 2] = x.z;
+        wd[4 * v + 3] = x.w;
+      }
+    } else if constexpr (WW % 2 == 0) {
+#pragma unroll
+      for (int v = 0; v < WW / 2; ++v) {
+        const uint2 x = reinterpret_cast<const uint2*>(p)[v];
+        wd[2 * v] = x.x;
+        wd[2 * v + 1] = x.y;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < WW; ++v) wd[v] = p[v];
+    }
+  }
   // The three values of sphere s: one segment check, then one 32-bit
-  // shared load per value.
+  // shared load per value (the formats without a window, below).
   template <int K>
   __device__ __forceinline__ void sphere(int s, const DevFmt& f, float& g0_, float& g1_, float& g2_) {
     while (s >= s_end) advance_to(cur + 1);  // spheres come in increasing order
@@ -196,8 +238,55 @@ struct SegReader {
   }
 };
 
-// GK: format kind of the gradient rows (the hot input), fixed at compile time.
-template <int GK>
+// Windows: WS whole spheres whose 3 WS values fill WW whole words (k values
+// per word, fixed at compile time: GKW for the generic kind); a segment
+// holds WPS windows.  A window's words are read at once and decoded with
+// every bit position fixed at compile time.
+template <int GK, int GKW>
+constexpr int values_per_word() {
+  if constexpr (GK == KIND_GENERIC) return GKW;  // 0: runtime
+  else return Fmt<GK>::k;
+}
+template <int GK, int GKW = 0>
+struct Win {
+  static constexpr int k = values_per_word<GK, GKW>();
+  // the fewest whole spheres that fill whole words: 3 WS a multiple of k
+  static constexpr int WS = k == 8 ? 8 : k == 5 ? 5 : k == 6 ? 2 : k == 3 ? 1 : 4;
+  static constexpr bool ok = k >= 1 && k <= 8 && k != 7;
+  static constexpr int WW = ok ? 3 * WS / k : 1;
+  static constexpr int WPS = SEG_W / WW;
+  static_assert(!ok || (3 * WS) % k == 0, "a window holds whole words");
+  static_assert(!ok || SEG_W % WW == 0, "a segment holds whole windows");
+};
+
+// Values 0 .. 3 WS - 1 of a window's words.
+template <int GK, int WS, int WW>
+__device__ __forceinline__ void decode_window(const uint32_t (&wd)[WW], float (&v)[3 * WS], const DevFmt& f) {
+  constexpr int k = 3 * WS / WW;
+  if constexpr (GK == KIND_GENERIC) {
+#pragma unroll
+    for (int i = 0; i < 3 * WS; ++i) v[i] = decode_generic((wd[i / k] >> (f.bits * (i % k))) & f.mask, f);
+  } else if constexpr (k == 1) {
+#pragma unroll
+    for (int i = 0; i < 3 * WS; ++i) v[i] = __uint_as_float(wd[i]);
+  } else {
+    constexpr int b = Fmt<GK>::bits;
+    constexpr uint32_t m = (1u << b) - 1u;
+#pragma unroll
+    for (int w = 0; w < WW; ++w) {  // the k values of each word, two at a time
+#pragma unroll
+      for (int r = 0; r < k; r += 2) {
+        const float2 x = dec_pair<GK>((wd[w] >> (b * r)) & m, r + 1 < k ? (wd[w] >> (b * (r + 1))) & m : 0u);
+        v[w * k + r] = x.x;
+        if (r + 1 < k) v[w * k + r + 1] = x.y;
+      }
+    }
+  }
+}
+
+// GK: format kind of the gradient rows (the hot input), fixed at compile
+// time; GKW: values per word of a generic kind (0: runtime).
+template <int GK, int GKW>
 __global__ void __launch_bounds__(BW_BLOCK, 4) backward_kernel(BwArgs a) {
   extern __shared__ float4 smem4[];
   const int J = a.r.J;
@@ -220,16 +309,8 @@ __global__ void __launch_bounds__(BW_BLOCK, 4) backward_kernel(BwArgs a) {
   const int64_t first = (int64_t)blockIdx.x * BW_WARPS + warp, step = (int64_t)gridDim.x * BW_WARPS;
   const int64_t my_tiles = first < n_tiles ? (n_tiles - 1 - first) / step + 1 : 0;
   SegReader sr;
-  sr.slots = ring + (size_t)warp * SEG_SLOTS * SEG_BYTES;
-  sr.rows = a.grad.ptr;
-  sr.stride = a.grad.stride;
-  sr.n = a.n;
-  sr.nseg = (int)((3 * a.r.S + 12 * a.grad.f.k - 1) / (12 * a.grad.f.k));
-  sr.lane = lane;
-  sr.kw = a.grad.f.k;
-  sr.first = first;
-  sr.step = step;
-  sr.total = use_ring ? my_tiles * sr.nseg : 0;
+  sr.init(ring + (size_t)warp * SEG_SLOTS * SEG_BYTES, a.grad.ptr, a.grad.stride, a.n, a.r.S, a.grad.f.k, lane,
+          first, step, use_ring ? my_tiles : 0);
   if (a.q && my_tiles > 0) q_prefetch(qbuf, a.q, first * 32, a.n, J, lane);
   grid_dependents_may_launch();
   grid_dependency_wait();  // the gradient rows are complete from here on
@@ -254,7 +335,31 @@ __global__ void __launch_bounds__(BW_BLOCK, 4) backward_kernel(BwArgs a) {
     RowReader<ROW_GLOBAL_RO> x{a.xform.ptr && live ? a.xform.ptr + c * a.xform.stride : nullptr};
     auto put = [&](int j, float v) { myK[32 * (2 * j + 1)].w = v; };  // after b_j is read
     if (use_ring) {
-      backward_config<GK>(rb, J, live, qp, x, a.xform.f, sr, a.grad.f, dc, myK, 32, put);
+      if constexpr (Win<GK, GKW>::ok) {
+        // link j's spheres [s0, s1) by windows: every window that holds one
+        // of them, with the others of the window left out (warp-uniform)
+        using W = Win<GK, GKW>;
+        backward_chain(rb, J, live, qp, x, a.xform.f, dc, myK, 32, [&](int j, LinkSums& ls) {
+          const int s0 = rb.start[j], s1 = rb.start[j + 1];
+          if (s0 < s1) {
+            for (int wdx = s0 / W::WS; wdx * W::WS < s1; ++wdx) {
+              const int seg = wdx / W::WPS;
+              sr.advance_to(seg);
+              uint32_t wd[W::WW];
+              sr.window<W::WW>(wdx - seg * W::WPS, wd);
+              float v[3 * W::WS];
+              decode_window<GK, W::WS, W::WW>(wd, v, a.grad.f);
+#pragma unroll
+              for (int u = 0; u < W::WS; ++u) {
+                const int sp = wdx * W::WS + u;
+                if (sp >= s0 && sp < s1) ls.add(v[3 * u], v[3 * u + 1], v[3 * u + 2], rb.sph[sp]);
+              }
+            }
+          }
+        }, put);
+      } else {
+        backward_config<GK>(rb, J, live, qp, x, a.xform.f, sr, a.grad.f, dc, myK, 32, put);
+      }
       sr.end_tile();
     } else {
       RowReader<ROW_GLOBAL_RO> g{live ? a.grad.ptr + c * a.grad.stride : a.grad.ptr};
@@ -278,17 +383,25 @@ int backward_device_error(bool reset) {
   return v;
 }
 
-static void (*bw_kernel_for(int kind))(BwArgs) {
-  switch (kind) {
-    case KIND_F32: return backward_kernel<KIND_F32>;
-    case KIND_F16: return backward_kernel<KIND_F16>;
-    case KIND_BF16: return backward_kernel<KIND_BF16>;
-    case KIND_E4M3: return backward_kernel<KIND_E4M3>;
-    case KIND_E5M2: return backward_kernel<KIND_E5M2>;
-    case KIND_E2M1: return backward_kernel<KIND_E2M1>;
-    case KIND_E3M2: return backward_kernel<KIND_E3M2>;
-    case KIND_E2M3: return backward_kernel<KIND_E2M3>;
-    default: return backward_kernel<KIND_GENERIC>;
+static void (*bw_kernel_for(const DevFmt& f))(BwArgs) {
+  switch (f.kind) {
+    case KIND_F32: return backward_kernel<KIND_F32, 0>;
+    case KIND_F16: return backward_kernel<KIND_F16, 0>;
+    case KIND_BF16: return backward_kernel<KIND_BF16, 0>;
+    case KIND_E4M3: return backward_kernel<KIND_E4M3, 0>;
+    case KIND_E5M2: return backward_kernel<KIND_E5M2, 0>;
+    case KIND_E2M1: return backward_kernel<KIND_E2M1, 0>;
+    case KIND_E3M2: return backward_kernel<KIND_E3M2, 0>;
+    case KIND_E2M3: return backward_kernel<KIND_E2M3, 0>;
+    default:
+      switch (f.k) {  // the widths of the searched formats (4 to 16 bits)
+        case 2: return backward_kernel<KIND_GENERIC, 2>;
+        case 3: return backward_kernel<KIND_GENERIC, 3>;
+        case 4: return backward_kernel<KIND_GENERIC, 4>;
+        case 5: return backward_kernel<KIND_GENERIC, 5>;
+        case 6: return backward_kernel<KIND_GENERIC, 6>;
+        default: return backward_kernel<KIND_GENERIC, 0>;
+      }
   }
 }
 
@@ -302,7 +415,7 @@ cudaError_t launch_backward(const RobotArgs& r, const float* q, Packed xform, Pa
   a.grad = grad;
   a.jgrad = jgrad;
   a.dcost = dcost;
-  void (*kern)(BwArgs) = bw_kernel_for(grad.f.kind);
+  void (*kern)(BwArgs) = bw_kernel_for(grad.f);
   Bump b(nullptr);
   RobotSm rb;
   uint8_t* ring;

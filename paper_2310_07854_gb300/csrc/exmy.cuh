@@ -49,12 +49,15 @@ struct DevFmt {
   uint32_t max_code, inf_code, nan_code;
   int ovf_inf;            // overflow -> Inf (IEEE without saturation)
   int ieee, fn;
-  int fastdec;            // finite-only, all codes numeric, E < 8: decode by one multiply
+  int fastdec;            // finite-only, all codes numeric, E < 8: decode by one multiply,
+                          // and encode |x| >= 2^emin by one multiply and an integer rounding
   float dec_scale;        // 2^(127 - bias)
+  float enc_scale;        // 2^(bias - 127)
+  uint32_t enc_lo;        // float32 bits of 2^emin, the smallest normal value
 };
 
 // ------------------------------------------------------------ generic path
-__device__ __forceinline__ uint32_t encode_generic(float x, const DevFmt& f) {
+__device__ __forceinline__ uint32_t encode_exact(float x, const DevFmt& f) {
   const uint32_t u = __float_as_uint(x);
   const uint32_t a = u & 0x7fffffffu;
   if (a > 0x7f800000u) return f.nan_code;
@@ -83,6 +86,26 @@ __device__ __forceinline__ uint32_t encode_generic(float x, const DevFmt& f) {
   if (efield > f.emax_field || (efield == f.emax_field && mant > f.mmax))
     return sbit | (f.ovf_inf ? f.inf_code : f.max_code);
   return sbit | (efield << f.M) | mant;
+}
+
+// encode_exact's codes, faster for the finite formats with E < 8 (fastdec):
+// for |x| >= 2^emin (or 0), |x| 2^(bias - 127) is an exact float32 whose
+// exponent field is the format's, so rounding its bits to M mantissa bits
+// (an integer add of half a unit less one, plus the lowest kept bit: ties
+// to even, carries into the exponent included) gives the code's magnitude;
+// past the largest value it saturates, as the format does.  Values below
+// 2^emin (the format's subnormals), Inf and NaN take the exact path.
+__device__ __forceinline__ uint32_t encode_generic(float x, const DevFmt& f) {
+  if (f.fastdec) {
+    const uint32_t u = __float_as_uint(x), a = u & 0x7fffffffu;
+    if ((a == 0u || a >= f.enc_lo) && a < 0x7f800000u) {
+      const uint32_t y = __float_as_uint(__uint_as_float(a) * f.enc_scale);
+      const int sh = 23 - f.M;
+      const uint32_t mag = (y + ((1u << (sh - 1)) - 1u) + ((y >> sh) & 1u)) >> sh;
+      return ((u >> 31) << (f.E + f.M)) | (mag < f.max_code ? mag : f.max_code);
+    }
+  }
+  return encode_exact(x, f);
 }
 
 __device__ __forceinline__ float decode_generic(uint32_t code, const DevFmt& f) {

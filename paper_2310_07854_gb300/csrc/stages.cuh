@@ -133,18 +133,34 @@ __device__ inline void load_clusters(int J, int S, const RobotSm& r) {
 
 // ------------------------------------------------------------ FK (thread)
 // One step of the joint chain: (R, t) = T_{j-1} becomes T_j = T_{j-1} F_j Rz(q_j).
-// sin and cos of a joint angle: q reduced to [-pi, pi] as r = q - 2 pi k,
-// k the integer nearest q / 2 pi (Cody-Waite reduction: 2 pi split into its
-// float and the float of the remainder, each subtracted by one fused
-// multiply-add; r = q exactly for |q| <= pi, and r is off by far less than
-// the approximation error below for |q| up to thousands of radians), then
-// the hardware approximations, whose absolute error on [-pi, pi] is at most
-// 2^-21.4 (about 4e-7, under the float32 tolerance of the whole path).
+// sin and cos of a joint angle, to about one float32 ulp.  Cody-Waite
+// reduction to r = q - k pi/2 in [-pi/4, pi/4] (k the integer nearest
+// 2q/pi; pi/2 split into its float and the float of the remainder, each
+// subtracted by one fused multiply-add: exact first step for |k| < 2^21,
+// and r off by about 1e-15 |k| plus one rounding), then the Taylor series
+// of sin r to r^9 and of cos r to r^10, whose truncation errors on
+// [-pi/4, pi/4] are below 2e-9 and 2e-10, evaluated by Horner's rule; the
+// quadrant k mod 4 picks (sin, cos) = (s, c), (c, -s), (-s, -c), (-c, s).
 __device__ __forceinline__ void joint_sincos(float q, float& sn, float& cs) {
-  const float k = rintf(q * 0.159154943f);  // 1 / (2 pi)
-  float r = fmaf(-k, 6.28318548f, q);       // float(2 pi) = 2 pi + 1.7484555e-7
-  r = fmaf(k, 1.74845553e-7f, r);
-  __sincosf(r, &sn, &cs);
+  const float k = rintf(q * 0.636619772f);  // 2 / pi
+  float r = fmaf(-k, 1.57079637f, q);       // float(pi/2) = pi/2 + 4.3711388e-8
+  r = fmaf(k, 4.37113883e-8f, r);
+  const float r2 = r * r;
+  // sin r = r (1 - r^2/3! + r^4/5! - r^6/7! + r^8/9!)
+  float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);
+  ps = fmaf(r2, ps, 8.33333333e-3f);
+  ps = fmaf(r2, ps, -1.66666667e-1f);
+  const float sr = fmaf(r * r2, ps, r);
+  // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
+  float pc = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);
+  pc = fmaf(r2, pc, -1.38888889e-3f);
+  pc = fmaf(r2, pc, 4.16666667e-2f);
+  pc = fmaf(r2, pc, -0.5f);
+  const float cr = fmaf(r2, pc, 1.f);
+  const int quad = (int)k & 3;
+  const float s_ = (quad & 1) ? cr : sr, c_ = (quad & 1) ? sr : cr;
+  sn = (quad & 2) ? -s_ : s_;
+  cs = ((quad + 1) & 2) ? -c_ : c_;
 }
 
 __device__ __forceinline__ void joint_step(const RobotSm& r, int j, float qj, float (&R)[3][3], float (&t)[3]) {
@@ -928,14 +944,13 @@ __device__ __forceinline__ void joint_axis(const float (&R)[3][3], const float (
 // One pass over the links in chain order: at joint j the running totals
 // M, F hold links < j, so K_j = a_j . M - b_j . F, and at the end
 // J_j = (a_j . M - b_j . F) - K_j over all links (= links >= j).
-// live == false runs the same control flow (its results are not stored).
-// The gradient reader g gives the three values of a sphere (g.sphere); all
-// lanes of a warp ask for the same sphere at the same time (the sphere
-// order is the robot's, shared by all lanes).
-template <int GK, typename XR, typename GR, typename Put>
-__device__ __forceinline__ void backward_config(const RobotSm& rb, int J, bool live, const float* q, XR& x,
-                                                const DevFmt& fx, GR& g, const DevFmt& fg, float dc,
-                                                float4* myK, int kst, Put put) {
+// sums(j, ls) adds link j's spheres to ls (LinkSums, zeroed), in the
+// robot's sphere order.  live == false runs the same control flow (its
+// results are not stored).
+template <typename XR, typename Sums, typename Put>
+__device__ __forceinline__ void backward_chain(const RobotSm& rb, int J, bool live, const float* q, XR& x,
+                                               const DevFmt& fx, float dc, float4* myK, int kst, Sums sums,
+                                               Put put) {
   float R[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
   float t[3] = {0.f, 0.f, 0.f};
   float F[3] = {0.f, 0.f, 0.f}, M[3] = {0.f, 0.f, 0.f};
@@ -958,12 +973,7 @@ __device__ __forceinline__ void backward_config(const RobotSm& rb, int J, bool l
     myK[(2 * j + 1) * kst] = make_float4(bx, by, bz, 0.f);
     LinkSums ls;
     ls.zero();
-    for (int idx = rb.start[j]; idx < rb.start[j + 1]; ++idx) {
-      const int s = rb.order[idx];
-      float g0, g1, g2;
-      g.template sphere<GK>(s, fg, g0, g1, g2);
-      ls.add(g0, g1, g2, rb.sph[s]);
-    }
+    sums(j, ls);
     float mo[3];
     ls.moment(R, t, mo);
 #pragma unroll
@@ -976,6 +986,23 @@ __device__ __forceinline__ void backward_config(const RobotSm& rb, int J, bool l
     const float4 ak = myK[2 * j * kst], b = myK[(2 * j + 1) * kst];
     put(j, __fmul_rn(dc, __fsub_rn(axis_term(ak.x, ak.y, ak.z, b.x, b.y, b.z, M, F), ak.w)));
   }
+}
+
+// backward_chain with the gradient reader g, which gives the three values
+// of a sphere (g.sphere); all lanes of a warp ask for the same sphere at
+// the same time (the sphere order is the robot's, shared by all lanes).
+template <int GK, typename XR, typename GR, typename Put>
+__device__ __forceinline__ void backward_config(const RobotSm& rb, int J, bool live, const float* q, XR& x,
+                                                const DevFmt& fx, GR& g, const DevFmt& fg, float dc,
+                                                float4* myK, int kst, Put put) {
+  backward_chain(rb, J, live, q, x, fx, dc, myK, kst, [&](int j, LinkSums& ls) {
+    for (int idx = rb.start[j]; idx < rb.start[j + 1]; ++idx) {
+      const int s = rb.order[idx];
+      float g0, g1, g2;
+      g.template sphere<GK>(s, fg, g0, g1, g2);
+      ls.add(g0, g1, g2, rb.sph[s]);
+    }
+  }, put);
 }
 
 // Packed joint-gradient row of J values get(i) (padding words written as zero).

@@ -68,8 +68,13 @@ def test_unpack_decodes_every_code(f):
     assert np.array_equal(np.signbit(got[~nan]), np.signbit(want[~nan]))
 
 
+# generic formats whose encoder takes the one-multiply fast path (finite,
+# E < 8), two of them the searched table's G and J formats
+FAST_GENERIC = (F.fmt(6, 3), F.fmt(3, 4), F.fmt(2, 2), F.fmt(5, 4))
+
+
 @pytest.mark.slow
-@pytest.mark.parametrize("f", F.SWEEP, ids=str)
+@pytest.mark.parametrize("f", F.SWEEP + FAST_GENERIC, ids=str)
 def test_pack_all_float32_bit_patterns(f):
     """Every one of the 2^32 float32 inputs (65 chunks of 16448 rows x 4080;
     4080 is a multiple of every pack factor, the last chunk wraps around).
