@@ -112,7 +112,32 @@ typedef struct {
   const float* sphere_local;   /* [S][4]: x, y, z in the link frame, radius */
   const int32_t* sphere_link;  /* [S]: link index 1..J */
   const int32_t* pairs;        /* [n_pairs][2]: sphere indices */
+  const void* tables;          /* NULL, or tables that vapr_robot_tables_build
+                                  made for this robot (see there); they change
+                                  how fast a launch starts, never a result */
 } vapr_robot;
+
+/* ---- robot tables (robot preprocessing) ------------------------------------
+ * Every launch that runs the collision stage (vapr_collision_cost,
+ * vapr_cost_grad, vapr_cost_grad_noalloc, vapr_cost_grad_fused, the
+ * multi-problem launch) first lays out, in each block's shared memory, the
+ * robot's spheres grouped by link, its self-collision clusters (runs of up
+ * to 3 spheres of one link) and its self pairs grouped by cluster pair (the
+ * self-collision broad phase of iteration step 3, Sec. III-B).  Building
+ * that takes each block about 10 us for an arm with 832 pairs; with
+ * robot->tables set, the blocks copy tables built once instead.  Each
+ * launch checks on the device that the tables were built for the robot's
+ * current joint, sphere, link and pair words (a hash) and otherwise builds
+ * its own, so stale tables cost speed, never correctness.  The tables do
+ * not depend on the cost parameters. */
+/* bytes of the tables of `robot` (0 when the robot is invalid) */
+size_t vapr_robot_tables_bytes(const vapr_robot* robot);
+/* Builds the tables of `robot` (robot->tables is ignored) into `tables`
+ * (device memory, 16-byte aligned, bytes >= vapr_robot_tables_bytes);
+ * VAPR_ERR_INVALID_ARG when the buffer is missing or too small.
+ * Asynchronous on `stream`; the buffer is the caller's and must outlive the
+ * launches that use it. */
+vapr_status vapr_robot_tables_build(const vapr_robot* robot, void* tables, size_t bytes, void* stream);
 
 /* Oriented cuboids (device memory, 16-byte aligned). */
 typedef struct {

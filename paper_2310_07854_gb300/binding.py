@@ -55,7 +55,8 @@ class vapr_robot(ctypes.Structure):
     _fields_ = [("n_joints", ctypes.c_int32), ("n_spheres", ctypes.c_int32),
                 ("n_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("joint_fixed", ctypes.c_void_p), ("sphere_local", ctypes.c_void_p),
-                ("sphere_link", ctypes.c_void_p), ("pairs", ctypes.c_void_p)]
+                ("sphere_link", ctypes.c_void_p), ("pairs", ctypes.c_void_p),
+                ("tables", ctypes.c_void_p)]
 
 
 class vapr_scene(ctypes.Structure):
@@ -172,6 +173,8 @@ SIGNATURES = {
                                            _P, ctypes.c_size_t, _P, _P]),
     "vapr_scene_sdf": (ctypes.c_int, [ctypes.POINTER(vapr_scene), _P, _i64, _P, _P]),
     "vapr_scene_grid_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "vapr_robot_tables_bytes": (ctypes.c_size_t, [ctypes.POINTER(vapr_robot)]),
+    "vapr_robot_tables_build": (ctypes.c_int, [ctypes.POINTER(vapr_robot), _P, ctypes.c_size_t, _P]),
     "vapr_scene_grid_build": (ctypes.c_int, [ctypes.POINTER(vapr_scene), ctypes.c_float, ctypes.c_float,
                                              ctypes.c_int32, _P, ctypes.c_size_t, _P]),
     "vapr_surrogate_samples": (ctypes.c_int, [ctypes.POINTER(vapr_scene),
@@ -247,9 +250,11 @@ def _check(status: int, where: str):
 
 
 class DeviceRobot:
-    """Device copies of a ``synth.Robot`` and the ``vapr_robot`` pointing at them."""
+    """Device copies of a ``synth.Robot`` and the ``vapr_robot`` pointing at
+    them, with the robot's prebuilt tables attached (``tables=False``: none,
+    every launch builds its own)."""
 
-    def __init__(self, robot, device="cuda"):
+    def __init__(self, robot, device="cuda", tables=True):
         import torch
         self.host = robot
         self.joint_fixed = torch.as_tensor(np.ascontiguousarray(robot.joint_fixed, np.float32), device=device)
@@ -259,7 +264,26 @@ class DeviceRobot:
         self.pairs = torch.as_tensor(pairs if pairs.size else np.zeros((1, 2), np.int32), device=device)
         self.c = vapr_robot(robot.n_joints, robot.n_spheres, int(pairs.shape[0]), 0,
                             self.joint_fixed.data_ptr(), self.sphere_local.data_ptr(),
-                            self.sphere_link.data_ptr(), self.pairs.data_ptr())
+                            self.sphere_link.data_ptr(), self.pairs.data_ptr(), None)
+        self.tables = None
+        if tables:
+            self.build_tables()
+
+    def build_tables(self, stream=None):
+        """Builds the robot tables (``vapr_robot_tables_build``) and attaches
+        them (``vapr_robot.tables``)."""
+        import torch
+        nb = vapr_robot_tables_bytes(self)
+        buf = torch.empty(nb, dtype=torch.uint8, device=self.joint_fixed.device)
+        self.c.tables = None
+        vapr_robot_tables_build(self, buf, nb, stream)
+        self.tables = buf
+        self.c.tables = buf.data_ptr()
+        return self
+
+    def drop_tables(self):
+        self.tables = None
+        self.c.tables = None
 
     @property
     def n_joints(self):
@@ -555,6 +579,15 @@ def vapr_scene_grid_build(scene: DeviceScene, reach, eta, cells_per_axis, grid, 
     _check(_load().vapr_scene_grid_build(ctypes.byref(scene.c), float(reach), float(eta), int(cells_per_axis),
                                          _ptr(grid), int(grid_bytes), _stream(stream)),
            "vapr_scene_grid_build")
+
+
+def vapr_robot_tables_bytes(robot: "DeviceRobot") -> int:
+    return int(_load().vapr_robot_tables_bytes(ctypes.byref(robot.c)))
+
+
+def vapr_robot_tables_build(robot: "DeviceRobot", tables, nbytes, stream=None):
+    _check(_load().vapr_robot_tables_build(ctypes.byref(robot.c), _ptr(tables), int(nbytes), _stream(stream)),
+           "vapr_robot_tables_build")
 
 
 def surrogate_domain(lo, hi, pad, margin) -> vapr_surrogate_domain:

@@ -201,7 +201,8 @@ vapr_status check_robot(const vapr_robot* r, RobotArgs* out) {
   if (!r->joint_fixed || !r->sphere_local || !r->sphere_link) return VAPR_ERR_INVALID_ARG;
   if (r->n_pairs > 0 && !r->pairs) return VAPR_ERR_INVALID_ARG;
   if (!aligned(r->joint_fixed, 16) || !aligned(r->sphere_local, 16) ||
-      !aligned(r->sphere_link, 16) || (r->pairs && !aligned(r->pairs, 16)))
+      !aligned(r->sphere_link, 16) || (r->pairs && !aligned(r->pairs, 16)) ||
+      (r->tables && !aligned(r->tables, 16)))
     return VAPR_ERR_MISALIGNED;
   out->J = r->n_joints;
   out->S = r->n_spheres;
@@ -210,6 +211,7 @@ vapr_status check_robot(const vapr_robot* r, RobotArgs* out) {
   out->sphere_local = r->sphere_local;
   out->sphere_link = r->sphere_link;
   out->pairs = r->pairs;
+  out->tables = r->tables;
   return VAPR_OK;
 }
 
@@ -248,6 +250,22 @@ static Packed packed(const void* p, int64_t row_len, vapr_format f) {
 using namespace vapr;
 
 extern "C" {
+
+size_t vapr_robot_tables_bytes(const vapr_robot* robot) {
+  RobotArgs r;
+  if (check_robot(robot, &r) != VAPR_OK) return 0;
+  return robot_tables_bytes(r);
+}
+
+vapr_status vapr_robot_tables_build(const vapr_robot* robot, void* tables, size_t bytes, void* stream) {
+  RobotArgs r;
+  const vapr_status st = check_robot(robot, &r);
+  if (st != VAPR_OK) return st;
+  if (!tables) return VAPR_ERR_INVALID_ARG;
+  if (!aligned(tables, 16)) return VAPR_ERR_MISALIGNED;
+  if (bytes < robot_tables_bytes(r)) return VAPR_ERR_INVALID_ARG;
+  return launch_robot_tables(r, tables, (cudaStream_t)stream) == cudaSuccess ? VAPR_OK : VAPR_ERR_CUDA;
+}
 
 const char* vapr_status_string(vapr_status s) {
   switch (s) {

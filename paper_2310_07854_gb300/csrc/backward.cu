@@ -349,10 +349,16 @@ __global__ void __launch_bounds__(BW_BLOCK, 4) backward_kernel(BwArgs a) {
               sr.window<W::WW>(wdx - seg * W::WPS, wd);
               float v[3 * W::WS];
               decode_window<GK, W::WS, W::WW>(wd, v, a.grad.f);
+              const int w0 = wdx * W::WS;
+              if (w0 >= s0 && w0 + W::WS <= s1) {  // the whole window is on the link
 #pragma unroll
-              for (int u = 0; u < W::WS; ++u) {
-                const int sp = wdx * W::WS + u;
-                if (sp >= s0 && sp < s1) ls.add(v[3 * u], v[3 * u + 1], v[3 * u + 2], rb.sph[sp]);
+                for (int u = 0; u < W::WS; ++u) ls.add(v[3 * u], v[3 * u + 1], v[3 * u + 2], rb.sph[w0 + u]);
+              } else {
+#pragma unroll
+                for (int u = 0; u < W::WS; ++u) {
+                  const int sp = w0 + u;
+                  if (sp >= s0 && sp < s1) ls.add(v[3 * u], v[3 * u + 1], v[3 * u + 2], rb.sph[sp]);
+                }
               }
             }
           }

@@ -150,11 +150,8 @@ __global__ void __launch_bounds__(BT_BLOCK) batched_kernel(BatchArgs a) {
     const ProblemDev& P = a.probs[it.problem];
     const int J = P.r.J, S = P.r.S, rows = it.rows;
     if (it.problem != cur) {  // this problem's arm and obstacles into shared memory
-      load_robot(P.r, rb);
       load_scene(P.r, P.sc, P.eta, P.eta_s, sm);
-      __syncthreads();
-      load_clusters(J, S, rb);
-      load_self(P.r, rb, sm, self_scr, P.eta_s);
+      load_robot_self(P.r, rb, sm, self_scr, P.eta_s);
       init_coll_warp(P.r, w, lane);
       grid = grid_check(P.sc, P.r, P.eta);  // block-wide; null: every cuboid
       cells = grid ? grid_cells(P.sc) : nullptr;

@@ -21,9 +21,11 @@
 // them alone, in the same order.
 //
 // Self pairs: the block groups the pair table by cluster pair (runs of up to
-// three spheres of one link, load_self); per configuration, cluster pairs
-// whose bounding spheres are apart are skipped and the pairs of the others
-// tested in table order (self_pairs in stages.cuh).
+// three spheres of one link, load_self), or copies the robot's prebuilt
+// tables (load_robot_self: a hash-checked copy instead of about 10 us of
+// building per block); per configuration, cluster pairs whose bounding
+// spheres are apart are skipped and the pairs of the others tested in
+// table order (self_pairs in stages.cuh).
 //
 // Determinism: every sphere adds its terms in cuboid order in one register,
 // and a skipped pair would have added exactly zero, so the result of a
@@ -96,11 +98,8 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
   CollWarp w;
   SelfScratch scratch;
   carve_coll(b, a.r, a.sc.O, rb, sm, w, wid, scratch);
-  load_robot(a.r, rb);
   load_scene(a.r, a.sc, a.eta, a.eta_s, sm);
-  __syncthreads();
-  load_clusters(a.r.J, a.r.S, rb);
-  load_self(a.r, rb, sm, scratch, a.eta_s);
+  load_robot_self(a.r, rb, sm, scratch, a.eta_s);
   init_coll_warp(a.r, w, lane);
   __syncthreads();
   const GridHeader* grid = grid_check(a.sc, a.r, a.eta);  // null: visit every cuboid

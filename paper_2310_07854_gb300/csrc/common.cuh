@@ -17,6 +17,7 @@ struct RobotArgs {
   const float* sphere_local;  // [S][4]
   const int32_t* sphere_link; // [S]
   const int32_t* pairs;       // [NP][2]
+  const void* tables = nullptr;  // prebuilt self-collision tables (stages.cuh), or null
 };
 
 struct SceneArgs {
@@ -48,6 +49,8 @@ int sm_count();  // SMs of the current device (cached per device)
 // the kernel's dynamic shared-memory limit; later calls hit a cache, so a
 // launch costs no attribute or occupancy query.  Returns <= 0 on error.
 int blocks_per_sm(const void* fn, int threads, size_t smem);
+size_t robot_tables_bytes(const RobotArgs& r);
+cudaError_t launch_robot_tables(RobotArgs r, void* out, cudaStream_t st);
 
 int backward_device_error(bool reset);  // sticky device word of vapr_backward
 int tc_device_error(bool reset);        // sticky device word of the tensor-core kernels

@@ -98,11 +98,8 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
   FusedWarp fw;
   SelfScratch scratch;
   carve_fused(b, a, rb, sm, w, fw, wid, scratch);
-  load_robot(a.r, rb);
   load_scene(a.r, a.sc, a.eta, a.eta_s, sm);
-  __syncthreads();
-  load_clusters(J, S, rb);
-  load_self(a.r, rb, sm, scratch, a.eta_s);
+  load_robot_self(a.r, rb, sm, scratch, a.eta_s);
   init_coll_warp(a.r, w, lane);
   __shared__ int s_next;
   if (threadIdx.x == 0) s_next = 0;

@@ -413,6 +413,119 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
   __syncthreads();
 }
 
+// ------------------------------------------------- prebuilt robot tables
+// What load_robot, load_clusters and load_self build in shared memory
+// depends on the robot alone, but for the self-pair thresholds
+// r_i + r_j + eta_s: vapr_robot_tables_build stores it once in global
+// memory (RobotImage: a header, then the shared-memory arrays in the same
+// order and 16-byte alignment, thresholds without eta_s), and a block
+// whose robot carries such tables copies them (load_robot_self) instead of
+// building them, after checking that they were made for the robot's
+// current contents (a hash of its arrays, as the scene grid is checked).
+// A threshold (r_i + r_j) + eta_s is rounded as load_self rounds it, so
+// copied and built tables are the same bytes.
+constexpr uint32_t TABLES_MAGIC = 0x56525442u;
+
+struct TablesHeader {
+  uint32_t magic, J, S, NP, hash, NG;
+  uint32_t pad[10];  // 64 bytes
+};
+static_assert(sizeof(TablesHeader) == 64, "the arrays after the header stay 16-byte aligned");
+
+struct RobotImage {
+  TablesHeader* h;
+  RobotSm rb;
+  uint2* pairs;
+  uint16_t* cp;
+  uint16_t* cp_start;
+};
+
+__host__ __device__ inline void carve_image(Bump& b, int J, int S, int NP, RobotImage& im) {
+  im.h = b.take<TablesHeader>(1);
+  carve_robot(b, J, S, im.rb);
+  const int NG = pair_groups_bound(NP, cluster_bound(S, J));
+  im.pairs = b.take<uint2>(NP);
+  im.cp = b.take<uint16_t>(NG);
+  im.cp_start = b.take<uint16_t>(NG + 1);
+}
+
+// Hash of the robot's arrays (and sizes): the sum over words of
+// mix(word, i), as the scene grid's hash.
+__device__ __forceinline__ uint32_t robot_hash_part(const RobotArgs& r, int tid, int stride) {
+  uint32_t s = 0;
+  const int n0 = 12 * r.J, n1 = n0 + 4 * r.S, n2 = n1 + r.S, nw = n2 + 2 * r.NP;
+  for (int i = tid; i < nw; i += stride) {
+    const uint32_t w = i < n0   ? __float_as_uint(r.joint_fixed[i])
+                       : i < n1 ? __float_as_uint(r.sphere_local[i - n0])
+                       : i < n2 ? (uint32_t)r.sphere_link[i - n1]
+                                : (uint32_t)r.pairs[i - n2];
+    s += fmix32(w ^ fmix32((uint32_t)i * 0x9e3779b9u + 0x7f4a7c15u));
+  }
+  if (tid == 0) s += fmix32((uint32_t)r.J * 0x01000193u ^ (uint32_t)r.S << 8 ^ (uint32_t)r.NP << 16);
+  return s;
+}
+
+// 16-byte granules of an array (its padding to 16 bytes included).
+__device__ __forceinline__ void copy_granules(void* dst, const void* src, size_t bytes) {
+  const int n = (int)((bytes + 15) / 16);
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    reinterpret_cast<uint4*>(dst)[i] = __ldg(reinterpret_cast<const uint4*>(src) + i);
+}
+
+// Block-cooperative (every thread calls it, the block converged): rb
+// (load_robot, load_clusters) and m's self tables (load_self) for eta_s,
+// copied from r.tables when they were made for this robot, else built.
+// Ends with the block synchronised.
+__device__ inline void load_robot_self(const RobotArgs& r, const RobotSm& rb, const SceneSm& m,
+                                       const SelfScratch& t, float eta_s) {
+  __shared__ uint32_t s_hash;
+  __shared__ int s_ok;
+  const TablesHeader* h = static_cast<const TablesHeader*>(r.tables);
+  bool ok = false;
+  if (h) {  // uniform over the block
+    if (threadIdx.x == 0) s_hash = 0u;
+    __syncthreads();
+    atomicAdd(&s_hash, robot_hash_part(r, threadIdx.x, blockDim.x));
+    __syncthreads();
+    if (threadIdx.x == 0)
+      s_ok = h->magic == TABLES_MAGIC && h->J == (uint32_t)r.J && h->S == (uint32_t)r.S &&
+             h->NP == (uint32_t)r.NP && h->hash == s_hash;
+    __syncthreads();
+    ok = s_ok != 0;
+  }
+  if (!ok) {
+    load_robot(r, rb);
+    __syncthreads();
+    load_clusters(r.J, r.S, rb);
+    load_self(r, rb, m, t, eta_s);
+    return;
+  }
+  Bump b(const_cast<void*>(r.tables));
+  RobotImage im;
+  carve_image(b, r.J, r.S, r.NP, im);
+  const int J = r.J, S = r.S, NCB = cluster_bound(S, J), NG = (int)h->NG;
+  copy_granules(rb.F, im.rb.F, 3 * J * sizeof(float4));
+  copy_granules(rb.sph, im.rb.sph, S * sizeof(float4));
+  copy_granules(rb.link0, im.rb.link0, S * sizeof(int));
+  copy_granules(rb.order, im.rb.order, S * sizeof(int));
+  copy_granules(rb.start, im.rb.start, (J + 1) * sizeof(int));
+  copy_granules(rb.cl_start, im.rb.cl_start, (NCB + 1) * sizeof(int));
+  copy_granules(rb.cl_of, im.rb.cl_of, S * sizeof(int));
+  copy_granules(rb.cl_sph, im.rb.cl_sph, NCB * sizeof(int));
+  copy_granules(rb.n_cl, im.rb.n_cl, sizeof(int));
+  copy_granules(m.cp, im.cp, NG * sizeof(uint16_t));
+  copy_granules(m.cp_start, im.cp_start, (NG + 1) * sizeof(uint16_t));
+  for (int p = threadIdx.x; p < r.NP; p += blockDim.x) {
+    const uint2 pr = __ldg(im.pairs + p);
+    m.pairs[p] = make_uint2(pr.x, __float_as_uint(__uint_as_float(pr.y) + eta_s));
+  }
+  if (threadIdx.x == 0) {
+    m.self_meta[0] = NG;
+    m.self_meta[1] = (int)__float_as_uint(eta_s);
+  }
+  __syncthreads();
+}
+
 // One warp's working set for one configuration.
 struct CollWarp {
   float4* P;       // [S] (x, y, z, r)
@@ -694,16 +807,15 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
       while (am) {
         const int e = __ffs(am) - 1;
         am &= am - 1u;
-        if (lane == e) {
-          float4 ai = w.acc[i];
+        if (lane == e) {  // both loads before either store (a pair with i == j has u = 0)
+          float4 ai = w.acc[i], aj = w.acc[j];
           ai.y -= ux;
           ai.z -= uy;
           ai.w -= uz;
-          w.acc[i] = ai;
-          float4 aj = w.acc[j];
           aj.y += ux;
           aj.z += uy;
           aj.w += uz;
+          w.acc[i] = ai;
           w.acc[j] = aj;
         }
         __syncwarp();

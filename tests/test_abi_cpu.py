@@ -370,3 +370,25 @@ def test_missing_library_fails_loudly():
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120, cwd=root)
     assert r.returncode == 0, r.stderr[-2000:]
     assert "raised: libvapr.so is missing" in r.stdout
+
+
+def test_robot_tables_argument_checks():
+    """vapr_robot_tables_bytes / _build reject bad robots and buffers on the
+    host (no device work on these paths); a misaligned tables pointer on a
+    robot is rejected by every entry point's robot check."""
+    lib = B.lib()
+    byref = ctypes.byref
+    INVALID, MIS = 1, 3
+    r = _robot_struct()
+    nb = lib.vapr_robot_tables_bytes(byref(r))
+    assert nb > 0 and nb % 16 == 0
+    # more pairs, more bytes; a bad robot has none
+    assert lib.vapr_robot_tables_bytes(byref(_robot_struct(n_pairs=100))) > nb
+    assert lib.vapr_robot_tables_bytes(byref(_robot_struct(n_joints=0))) == 0
+    assert lib.vapr_robot_tables_bytes(None) == 0
+    assert lib.vapr_robot_tables_build(byref(r), None, nb, None) == INVALID
+    assert lib.vapr_robot_tables_build(byref(r), 4104, nb, None) == MIS
+    assert lib.vapr_robot_tables_build(byref(r), 4096, nb - 16, None) == INVALID
+    assert lib.vapr_robot_tables_build(byref(_robot_struct(n_spheres=0)), 4096, nb, None) == INVALID
+    t = B.to_c_table(F.FP32_TABLE)
+    assert lib.vapr_fk(byref(_robot_struct(tables=4100)), 256, 4, byref(t), 256, None, None) == MIS
