@@ -199,8 +199,10 @@ def time_steps(ev, q, n, steps, warmup, flush_buf, torch):
     stage calls with external events captured between them (which keeps the
     kernels from overlapping; its step time is kept as step_three_calls).
     CUDA events on the launching stream bracket each replay; the L2 flush
-    runs before it, outside the events."""
+    runs before it, outside the events (none when flush_buf is None: inputs
+    larger than L2)."""
     st = torch.cuda.current_stream()
+    flush_buf = flush_buf if flush_buf is not None else torch.zeros(1, device="cuda")
     g, inner = ev.capture(q, n, timing_events=True)
     per = {"fk": [], "collision": [], "backward": [], "step": [], "step_three_calls": []}
     e0 = torch.cuda.Event(enable_timing=True)
@@ -434,8 +436,12 @@ def search_tables(w, ev32, args):
 def dram_sweep(w, robot_dev, tables, flush, torch, peaks, exps=range(15, 21), counts=(8, 40)):
     """Per-stage time and HBM fraction from 2^15 to 2^20 configurations, with
     the 8-cuboid scene of the single-problem workload and the 40-cuboid
-    scene of the benchmark, for each format table; L2 flushed before every
-    step (median of 3 steps after 2 untimed)."""
+    scene of the benchmark, for each format table (median of 3 steps after 2
+    untimed).  L2 is flushed before every step while a step's tensors fit in
+    twice the L2 size; beyond that the inputs themselves are larger than L2
+    and no flush runs (a flush by writing leaves the L2 full of dirty lines,
+    whose write-back the next kernel would pay)."""
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
     from paper_2310_07854_gb300.path import Evaluator
     nmax = 1 << max(exps)
     qmax = torch.as_tensor(synth.make_q(77, nmax), device="cuda")
@@ -448,9 +454,11 @@ def dram_sweep(w, robot_dev, tables, flush, torch, peaks, exps=range(15, 21), co
             bp = ev.bytes_per_config()
             for e in exps:
                 n = 1 << e
-                per = time_steps(ev, qmax, n, 3, 2, flush, torch)
+                big = sum(bp[k] for k in ("fk", "collision", "backward")) * n > 2 * l2
+                per = time_steps(ev, qmax, n, 3, 2, None if big else flush, torch)
                 row = {"cuboids": O, "table": tname, "n_configs": n,
-                       "configs_per_s": n / (statistics.median(per["step"]) / 1000.0)}
+                       "configs_per_s": n / (statistics.median(per["step"]) / 1000.0),
+                       "l2": "inputs larger than L2, no flush" if big else "flushed before every step"}
                 for k in ("fk", "collision", "backward"):
                     ms = statistics.median(per[k])
                     row[k] = {"ms": ms, "hbm_frac": bp[k] * n / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]}

@@ -531,12 +531,14 @@ struct CollWarp {
   float4* P;       // [S] (x, y, z, r)
   float4* acc;     // [S] (D, gx, gy, gz)
   float4* cls;     // [NC] cluster bounding spheres of this configuration (centre, radius)
+  float4* stage;   // [32] a round's active self pairs (i | j << 16, u), in lane order
 };
 
 __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp& w) {
   w.P = b.take<float4>(S);
   w.acc = b.take<float4>(S);
   w.cls = b.take<float4>(cluster_bound(S, J));
+  w.stage = b.take<float4>(32);
 }
 
 // Radii into P[].w and zero accumulators (once per robot).
@@ -797,29 +799,37 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
         }
       }
       // active pairs in table order (lane order within the chunk), one at a
-      // time: the pair's own lane updates both spheres' gradients, so every
-      // sphere receives its self terms in that order.  (Updating all at once
-      // when no two active pairs of a chunk share a sphere was measured and
-      // is slower, as is listing the kept cluster pairs of all chunks first
-      // and expanding them together.)
-      unsigned am = __ballot_sync(FULL_MASK, act);
-      if (act) selfsum += pen;
-      while (am) {
-        const int e = __ffs(am) - 1;
-        am &= am - 1u;
-        if (lane == e) {  // both loads before either store (a pair with i == j has u = 0)
-          float4 ai = w.acc[i], aj = w.acc[j];
-          ai.y -= ux;
-          ai.z -= uy;
-          ai.w -= uz;
-          aj.y += ux;
-          aj.z += uy;
-          aj.w += uz;
-          w.acc[i] = ai;
-          w.acc[j] = aj;
-        }
-        __syncwarp();
+      // time, so every sphere receives its self terms in that order: the
+      // active lanes stage their pairs in lane order and lane 0 applies
+      // them (one divergent region and two warp barriers per round, not per
+      // pair).  (Measured and slower: each pair's own lane applying it,
+      // behind a warp barrier per pair; the owners of the spheres
+      // accumulating in registers from shuffled pairs; updating all at once
+      // when no two active pairs of a chunk share a sphere; listing the kept
+      // cluster pairs of all chunks first and expanding them together.)
+      const unsigned am = __ballot_sync(FULL_MASK, act);
+      if (act) {
+        selfsum += pen;
+        w.stage[__popc(am & ((1u << lane) - 1u))] = make_float4(__int_as_float(i | (j << 16)), ux, uy, uz);
       }
+      __syncwarp();
+      if (lane == 0) {
+        const int na = __popc(am);
+        for (int k = 0; k < na; ++k) {
+          const float4 e = w.stage[k];
+          const int pi = __float_as_int(e.x) & 0xffff, pj = __float_as_int(e.x) >> 16;
+          float4 ai = w.acc[pi], aj = w.acc[pj];  // both loads first (a pair with i == j has u = 0)
+          ai.y -= e.y;
+          ai.z -= e.z;
+          ai.w -= e.w;
+          aj.y += e.y;
+          aj.z += e.z;
+          aj.w += e.w;
+          w.acc[pi] = ai;
+          w.acc[pj] = aj;
+        }
+      }
+      __syncwarp();
     }
   }
   __syncwarp();
