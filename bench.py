@@ -60,7 +60,7 @@ def parse_args():
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the learned-surrogate leg (training + gated collision)")
     ap.add_argument("--surrogate-epochs", type=int, default=80)
-    ap.add_argument("--kernel", choices=["fk", "collision", "backward", "mlp_infer", "step", "ceiling"],
+    ap.add_argument("--kernel", choices=["fk", "collision", "backward", "mlp_infer", "step", "fused", "ceiling"],
                     default=None,
                     help="profiling mode: run only this stage (--warmup launches, then --steps timed) on "
                          "--configs configurations of the workload and print its CUDA-event time")
@@ -456,9 +456,15 @@ def dram_sweep(w, robot_dev, tables, flush, torch, peaks, exps=range(15, 21), co
                 n = 1 << e
                 big = sum(bp[k] for k in ("fk", "collision", "backward")) * n > 2 * l2
                 per = time_steps(ev, qmax, n, 3, 2, None if big else flush, torch)
+                if big:  # each stage alone, 5 back-to-back launches per graph (no launch gaps)
+                    for k, fn in (("fk", lambda: ev.fk(qmax, n)), ("collision", lambda: ev.collision(n)),
+                                  ("backward", lambda: ev.backward(qmax, n))):
+                        per[k] = time_reps(fn, 5, 3, torch)
                 row = {"cuboids": O, "table": tname, "n_configs": n,
                        "configs_per_s": n / (statistics.median(per["step"]) / 1000.0),
-                       "l2": "inputs larger than L2, no flush" if big else "flushed before every step"}
+                       "l2": ("inputs larger than L2: no flush; stage times from graphs of 5 back-to-back "
+                              "launches of the stage" if big else "flushed before every step; stage times from "
+                              "events between the stages of one step")}
                 for k in ("fk", "collision", "backward"):
                     ms = statistics.median(per[k])
                     row[k] = {"ms": ms, "hbm_frac": bp[k] * n / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]}
@@ -659,6 +665,30 @@ def fused_leg(w, ev32, q, n, vtable, args, flush, torch, sizes=(None, 1 << 20)):
     return out
 
 
+def time_reps(fn, reps, samples, torch):
+    """Device ms per call of fn(), from `samples` replays of a CUDA graph of
+    `reps` back-to-back calls (for inputs larger than L2: no flush)."""
+    st = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(samples):
+        e0.record(st)
+        g.replay()
+        e1.record(st)
+        st.synchronize()
+        ts.append(e0.elapsed_time(e1) / reps)
+    return ts
+
+
 def time_graph(fn, steps, warmup, flush_buf, torch):
     """Mean device ms of fn() captured in a CUDA graph, L2 flushed before
     each replay (outside the events)."""
@@ -805,8 +835,13 @@ def kernel_mode(args):
         ev = Evaluator(w.robot, w.scene, w.params, n, table)
         ev.fk(q, n)
         ev.collision(n)
-        fn = {"fk": lambda: ev.fk(q, n), "collision": lambda: ev.collision(n),
-              "backward": lambda: ev.backward(q, n), "step": lambda: ev.step(q, n)}[args.kernel]
+        if args.kernel == "fused":
+            cost = torch.empty(n, device="cuda")
+            jg = B.alloc_packed(n, w.robot.n_joints, table.jgrad)
+            fn = lambda: B.vapr_cost_grad_fused(ev.robot, ev.scene, w.params, q, n, table, None, cost, None, jg)
+        else:
+            fn = {"fk": lambda: ev.fk(q, n), "collision": lambda: ev.collision(n),
+                  "backward": lambda: ev.backward(q, n), "step": lambda: ev.step(q, n)}[args.kernel]
     for _ in range(args.warmup):
         fn()
     torch.cuda.synchronize()
