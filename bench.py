@@ -1017,6 +1017,13 @@ def main():
     sweep = None
     if not args.no_dram_scale:
         sweep = dram_sweep(w, ev32.robot, {"fp32": F.FP32_TABLE, "vapr": vtable}, flush, torch, peaks)
+        if "measured_ceiling" in roof:  # the same fraction at the sweep's largest batch (FP32, this scene)
+            big = [r for r in sweep if r["table"] == "fp32" and r["cuboids"] == w.scene.n_cuboids]
+            if big:
+                r = max(big, key=lambda r: r["n_configs"])
+                tf = collision_flops_per_config(w) * r["n_configs"] / (r["collision"]["ms"] / 1000.0) / 1e12
+                roof["measured_ceiling"]["at_largest_sweep_batch"] = {
+                    "n_configs": r["n_configs"], "achieved_tflops": tf, "frac": tf / roof["measured_ceiling"]["tflops"]}
     bases = None
     if rank == 0 and world == 1 and not args.no_config_baselines:
         bases = config_baselines(args, flush, torch)
