@@ -167,6 +167,83 @@ class Evaluator:
         run.graph = g
         return run
 
+    def host_pipeline(self, n: int):
+        """Streaming end to end from pinned host memory: returns run(batches),
+        where batches is a sequence of (q_host [n, J], cost_host [n],
+        jgrad_host [n, J]) pinned float32 tensors; run processes them in
+        order, each batch with its own host-to-device copy of q and
+        device-to-host copies of C and J, and returns once every result is on
+        the host.  Two batches are in flight: the path of batch k (one CUDA
+        graph: vapr_cost_grad and the J unpack) runs while the copy of batch
+        k+1's q and the copies of batch k-1's results move on streams of
+        their own, ordered by events; the two batches in flight use two
+        evaluators (this one and a twin sharing its robot, scene and table),
+        so no copy touches a buffer that a running kernel uses."""
+        torch = self.torch
+        J = self.robot.n_joints
+        dev = self.cost.device
+        evs = [self, self._twin(n)]
+        qd = [torch.empty((n, J), dtype=torch.float32, device=dev) for _ in range(2)]
+        sc, si, so = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        graphs = []
+        for b in range(2):
+            with torch.cuda.stream(sc):
+                qd[b].zero_()
+                evs[b].cost_grad(qd[b], n, None, sc)  # fills the launch caches
+                evs[b].unpack_jgrad(n, sc)
+            sc.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=sc):
+                evs[b].cost_grad(qd[b], n, None, sc)
+                evs[b].unpack_jgrad(n, sc)
+            graphs.append(g)
+        in_done = [torch.cuda.Event() for _ in range(2)]
+        comp_done = [torch.cuda.Event() for _ in range(2)]
+        out_done = [torch.cuda.Event() for _ in range(2)]
+
+        def run(batches):
+            for k, (qh, ch, jh) in enumerate(batches):
+                b = k & 1
+                if k >= 2:
+                    si.wait_event(comp_done[b])  # batch k-2's kernels have read qd[b]
+                with torch.cuda.stream(si):
+                    qd[b].copy_(qh, non_blocking=True)
+                in_done[b].record(si)
+                sc.wait_event(in_done[b])
+                if k >= 2:
+                    sc.wait_event(out_done[b])  # batch k-2's results are out of evs[b]
+                with torch.cuda.stream(sc):
+                    graphs[b].replay()
+                comp_done[b].record(sc)
+                so.wait_event(comp_done[b])
+                with torch.cuda.stream(so):
+                    ch.copy_(evs[b].cost[:n], non_blocking=True)
+                    jh.copy_(evs[b].jgrad_f32[:n], non_blocking=True)
+                out_done[b].record(so)
+            so.synchronize()
+        run.graphs = graphs
+        return run
+
+    def _twin(self, n: int):
+        """An evaluator for n configurations sharing this one's robot, scene,
+        parameters and table, with buffers of its own."""
+        t = object.__new__(Evaluator)
+        t.torch = self.torch
+        t.robot, t.scene, t.params = self.robot, self.scene, self.params
+        t.table, t.ctable, t.recompute_fk, t.n_max = self.table, self.ctable, self.recompute_fk, n
+        torch = self.torch
+        dev = self.cost.device
+        S, J = self.robot.n_spheres, self.robot.n_joints
+        t.pos = B.alloc_packed(n, 3 * S, self.table.pos, dev)
+        t.dist = B.alloc_packed(n, S, self.table.dist, dev)
+        t.grad = B.alloc_packed(n, 3 * S, self.table.grad, dev)
+        t.jgrad = B.alloc_packed(n, J, self.table.jgrad, dev)
+        t.xform = None if self.recompute_fk else B.alloc_packed(n, 12 * J, self.table.xform, dev)
+        t.cost = torch.empty(n, dtype=torch.float32, device=dev)
+        t.jgrad_f32 = torch.empty((n, J), dtype=torch.float32, device=dev)
+        t.workspace = B.alloc_workspace(self.robot, n, self.table, dev)
+        return t
+
     def bytes_per_config(self) -> dict:
         """Algorithmic bytes per configuration of each stage (packed rows,
         unpadded; robot and scene tables excluded)."""

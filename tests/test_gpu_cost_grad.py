@@ -81,3 +81,28 @@ def test_host_step_and_its_graph():
         c2, j2 = run()
         want_c, want_j = device_path(qn)
         assert torch.equal(c2, want_c) and torch.equal(j2, want_j), seed
+
+
+@pytest.mark.parametrize("batches", [1, 2, 5])
+def test_host_pipeline(batches):
+    """host_pipeline: every batch's C and J, copied out while the next
+    batch's kernels run, equal the device path's bytes for that batch's q
+    (distinct q per batch, distinct host buffers)."""
+    import torch
+    from paper_2310_07854_gb300.path import Evaluator
+    w = synth.make_workload("sweep_1024")
+    n, J = w.n, w.robot.n_joints
+    ev = Evaluator(w.robot, w.scene, w.params, n)
+    run = ev.host_pipeline(n)
+    qs = [synth.make_q(40 + k, n) for k in range(batches)]
+    bufs = []
+    for qn in qs:
+        qh = torch.as_tensor(qn).pin_memory()
+        ch = torch.full((n,), float("nan")).pin_memory()
+        jh = torch.full((n, J), float("nan")).pin_memory()
+        bufs.append((qh, ch, jh))
+    run(bufs)
+    ref = Evaluator(w.robot, w.scene, w.params, n)
+    for qn, (_, ch, jh) in zip(qs, bufs):
+        ref.cost_grad(to_dev(qn), n)
+        assert torch.equal(ch, ref.cost[:n].cpu()) and torch.equal(jh, ref.unpack_jgrad(n).cpu())
