@@ -615,6 +615,16 @@ template <bool COHERENT>
 __device__ __forceinline__ void load_centres(const uint32_t* prow, const DevFmt& fP, int S, float4* P,
                                              int lane) {
   const int nv = 3 * S;
+  if (fP.kind == KIND_F32) {  // float32: lane s takes sphere s's three words
+    for (int s = lane; s < S; s += 32) {
+      const uint32_t* r = prow + 3 * s;
+      float* d = reinterpret_cast<float*>(P + s);
+      d[0] = __uint_as_float(COHERENT ? __ldcg(r) : __ldg(r));
+      d[1] = __uint_as_float(COHERENT ? __ldcg(r + 1) : __ldg(r + 1));
+      d[2] = __uint_as_float(COHERENT ? __ldcg(r + 2) : __ldg(r + 2));
+    }
+    return;
+  }
   dispatch_kind(fP.kind, [&](auto kc) {
     constexpr int K = decltype(kc)::value;
     const int kw = per_word<K>(fP);
@@ -660,7 +670,16 @@ __device__ __forceinline__ void coll_reset(const CollWarp& w, int S, int lane) {
 __device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const DevFmt& fD, const DevFmt& fG,
                                              float w_c, float extra, const CollOut& out, int lane) {
   coll_cost_dist(w, S, fD, w_c, extra, out, lane);
-  if (out.grad) {
+  if (out.grad && fG.kind == KIND_F32) {  // float32: lane s writes sphere s's three words
+    for (int s = lane; s < S; s += 32) {
+      const float4 a = w.acc[s];
+      uint32_t* r = out.grad + 3 * s;
+      r[0] = __float_as_uint(a.y);
+      r[1] = __float_as_uint(a.z);
+      r[2] = __float_as_uint(a.w);
+    }
+    for (int wd = 3 * S + lane; wd < out.grad_words; wd += 32) out.grad[wd] = 0u;  // row padding
+  } else if (out.grad) {
     const int nv = 3 * S;
     dispatch_kind(fG.kind, [&](auto kc) {
       constexpr int K = decltype(kc)::value;
