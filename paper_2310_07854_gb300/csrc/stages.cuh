@@ -564,19 +564,20 @@ __device__ __forceinline__ float4 box_term_value(const SceneSm& m, int o, const 
   const float u0 = fabsf(x0) - H.x, u1 = fabsf(x1) - H.y, u2 = fabsf(x2) - H.z;
   const float v0 = fmaxf(u0, 0.f), v1 = fmaxf(u1, 0.f), v2 = fmaxf(u2, 0.f);
   const float n2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-  const bool outside = u0 > 0.f || u1 > 0.f || u2 > 0.f;
-  // inside: the face of the largest u (lowest axis on ties)
-  const int k = (u0 >= u1 && u0 >= u2) ? 0 : (u1 >= u2 ? 1 : 2);
   const float umax = fmaxf(u0, fmaxf(u1, u2));
+  const bool outside = umax > 0.f;  // some u > 0 (fmaxf passes over a NaN as the comparisons do)
   const float rs = n2 > 0.f ? rsqrtf(n2) : 0.f;  // 1/|max(u,0)|
   const float d = outside ? n2 * rs : umax;
   const float pen = c.w + eta - d;
   if (pen > 0.f) {
-    const float inv = outside ? rs : 0.f;
+    // outside: s v / |v| (s = sign of x, +1 at 0; a product with s is its
+    // sign bit on s v |v|^-1, so copysignf gives the same bits); inside: s
+    // on the face of the largest u (lowest axis on ties)
+    const int k = (u0 >= u1 && u0 >= u2) ? 0 : (u1 >= u2 ? 1 : 2);
     const float s0 = x0 >= 0.f ? 1.f : -1.f, s1 = x1 >= 0.f ? 1.f : -1.f, s2 = x2 >= 0.f ? 1.f : -1.f;
-    const float l0 = outside ? s0 * v0 * inv : (k == 0 ? s0 : 0.f);
-    const float l1 = outside ? s1 * v1 * inv : (k == 1 ? s1 : 0.f);
-    const float l2 = outside ? s2 * v2 * inv : (k == 2 ? s2 : 0.f);
+    const float l0 = outside ? copysignf(v0 * rs, s0) : (k == 0 ? s0 : 0.f);
+    const float l1 = outside ? copysignf(v1 * rs, s1) : (k == 1 ? s1 : 0.f);
+    const float l2 = outside ? copysignf(v2 * rs, s2) : (k == 2 ? s2 : 0.f);
     acc.x = pen;  // gradient of the hinge: -grad d, scaled by w_coll
     acc.y = -w_c * fmaf(A0.x, l0, fmaf(A1.x, l1, A2.x * l2));
     acc.z = -w_c * fmaf(A0.y, l0, fmaf(A1.y, l1, A2.y * l2));
