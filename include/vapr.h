@@ -405,9 +405,10 @@ vapr_status vapr_cost_grad(const vapr_robot* robot, const vapr_scene* scene,
  * all, against storing them in reduced formats, Sec. III-C).  P and G are
  * still rounded to table->pos and table->grad in registers, as storing and
  * loading them would.  Same arguments as vapr_cost_grad without the
- * workspace.  cost and the D rows equal vapr_cost_grad's bit for bit; the
- * joint gradient sums the same terms in another order (per link, then over
- * links) and agrees with it to float32 rounding. */
+ * workspace.  cost, the D rows and the joint gradient equal
+ * vapr_cost_grad's bit for bit (the same collision code on the same rounded
+ * centres, and the backward sums taken in the same order with the same
+ * operations). */
 vapr_status vapr_cost_grad_fused(const vapr_robot* robot, const vapr_scene* scene,
                                  const vapr_cost_params* params, const float* q, int64_t n,
                                  const vapr_format_table* table, const float* dcost, float* cost,
