@@ -527,11 +527,14 @@ __device__ inline void load_robot_self(const RobotArgs& r, const RobotSm& rb, co
 }
 
 // One warp's working set for one configuration.
+constexpr int KEPT_CAP = 128;  // cluster pairs tested before their kept ones are expanded
+
 struct CollWarp {
   float4* P;       // [S] (x, y, z, r)
   float4* acc;     // [S] (D, gx, gy, gz)
   float4* cls;     // [NC] cluster bounding spheres of this configuration (centre, radius)
   float4* stage;   // [32] a round's active self pairs (i | j << 16, u), in lane order
+  uint16_t* kept;  // [KEPT_CAP] kept cluster pairs, in table order
 };
 
 __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp& w) {
@@ -539,6 +542,7 @@ __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp&
   w.acc = b.take<float4>(S);
   w.cls = b.take<float4>(cluster_bound(S, J));
   w.stage = b.take<float4>(32);
+  w.kept = b.take<uint16_t>(KEPT_CAP);
 }
 
 // Radii into P[].w and zero accumulators (once per robot).
@@ -773,84 +777,99 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
   }
   __syncwarp();
   float selfsum = 0.f;
-  for (int g0 = 0; g0 < NG; g0 += 32) {
-    const int g = g0 + lane;
-    int cnt = 0, st = 0;
-    if (g < NG) {
-      const uint32_t ab = m.cp[g];
-      const float4 A = w.cls[ab & 0xffu], B = w.cls[ab >> 8];
-      const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
-      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float mag = fabsf(A.x) + fabsf(A.y) + fabsf(A.z) + fabsf(B.x) + fabsf(B.y) + fabsf(B.z);
-      const float rhs = A.w + B.w + eta_s + fmaf(4e-6f, mag + A.w + B.w, 1e-4f);
-      if (!(rhs <= 0.f || d2 >= rhs * rhs)) {  // kept
+  for (int G0 = 0; G0 < NG; G0 += KEPT_CAP) {
+    // the kept cluster pairs of the next KEPT_CAP, in table order, into w.kept
+    int K = 0;
+#pragma unroll
+    for (int q = 0; q < KEPT_CAP / 32; ++q) {
+      const int g = G0 + 32 * q + lane;
+      bool keep = false;
+      if (g < NG) {
+        const uint32_t ab = m.cp[g];
+        const float4 A = w.cls[ab & 0xffu], B = w.cls[ab >> 8];
+        const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float mag = fabsf(A.x) + fabsf(A.y) + fabsf(A.z) + fabsf(B.x) + fabsf(B.y) + fabsf(B.z);
+        const float rhs = A.w + B.w + eta_s + fmaf(4e-6f, mag + A.w + B.w, 1e-4f);
+        keep = !(rhs <= 0.f || d2 >= rhs * rhs);
+      }
+      const unsigned km = __ballot_sync(FULL_MASK, keep);
+      if (keep) w.kept[K + __popc(km & ((1u << lane) - 1u))] = (uint16_t)g;
+      K += __popc(km);
+    }
+    __syncwarp();
+    for (int k0 = 0; k0 < K; k0 += 32) {  // their pairs, 32 cluster pairs at a time
+      int cnt = 0, st = 0;
+      if (k0 + lane < K) {
+        const int g = w.kept[k0 + lane];
         st = m.cp_start[g];
         cnt = m.cp_start[g + 1] - st;
       }
-    }
-    const int incl = warp_scan(cnt, lane), excl = incl - cnt;
-    const int total = __shfl_sync(FULL_MASK, incl, 31);
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int v = t0 + lane;
-      int owner = 0;  // first lane whose inclusive count exceeds v
+      const int incl = warp_scan(cnt, lane), excl = incl - cnt;
+      const int total = __shfl_sync(FULL_MASK, incl, 31);
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int v = t0 + lane;
+        int owner = 0;  // first lane whose inclusive count exceeds v
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (__shfl_sync(FULL_MASK, incl, owner + step - 1) <= v) owner += step;
-      const int pst = __shfl_sync(FULL_MASK, st, owner), pex = __shfl_sync(FULL_MASK, excl, owner);
-      bool act = false;
-      float pen = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-      int i = 0, j = 0;
-      if (v < total) {
-        const uint2 pr = m.pairs[pst + v - pex];
-        i = (int)(pr.x & 0xffffu);
-        j = (int)(pr.x >> 16);
-        const float4 ci = w.P[i], cj = w.P[j];
-        const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float thr = __uint_as_float(pr.y);
-        if (d2 < thr * thr) {
-          const float rs = d2 > 0.f ? rsqrtf(d2) : 0.f;
-          pen = thr - d2 * rs;
-          act = pen > 0.f;
-          const float inv = w_s * rs;  // 0 at zero distance: no gradient
-          ux = dx * inv;
-          uy = dy * inv;
-          uz = dz * inv;
+        for (int step = 16; step > 0; step >>= 1)
+          if (__shfl_sync(FULL_MASK, incl, owner + step - 1) <= v) owner += step;
+        const int pst = __shfl_sync(FULL_MASK, st, owner), pex = __shfl_sync(FULL_MASK, excl, owner);
+        bool act = false;
+        float pen = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+        int i = 0, j = 0;
+        if (v < total) {
+          const uint2 pr = m.pairs[pst + v - pex];
+          i = (int)(pr.x & 0xffffu);
+          j = (int)(pr.x >> 16);
+          const float4 ci = w.P[i], cj = w.P[j];
+          const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float thr = __uint_as_float(pr.y);
+          if (d2 < thr * thr) {
+            const float rs = d2 > 0.f ? rsqrtf(d2) : 0.f;
+            pen = thr - d2 * rs;
+            act = pen > 0.f;
+            const float inv = w_s * rs;  // 0 at zero distance: no gradient
+            ux = dx * inv;
+            uy = dy * inv;
+            uz = dz * inv;
+          }
         }
-      }
-      // active pairs in table order (lane order within the chunk), one at a
-      // time, so every sphere receives its self terms in that order: the
-      // active lanes stage their pairs in lane order and lane 0 applies
-      // them (one divergent region and two warp barriers per round, not per
-      // pair).  (Measured and slower: each pair's own lane applying it,
-      // behind a warp barrier per pair; the owners of the spheres
-      // accumulating in registers from shuffled pairs; updating all at once
-      // when no two active pairs of a chunk share a sphere; listing the kept
-      // cluster pairs of all chunks first and expanding them together.)
-      const unsigned am = __ballot_sync(FULL_MASK, act);
-      if (act) {
-        selfsum += pen;
-        w.stage[__popc(am & ((1u << lane) - 1u))] = make_float4(__int_as_float(i | (j << 16)), ux, uy, uz);
-      }
-      __syncwarp();
-      if (lane == 0) {
-        const int na = __popc(am);
-        for (int k = 0; k < na; ++k) {
-          const float4 e = w.stage[k];
-          const int pi = __float_as_int(e.x) & 0xffff, pj = __float_as_int(e.x) >> 16;
-          float4 ai = w.acc[pi], aj = w.acc[pj];  // both loads first (a pair with i == j has u = 0)
-          ai.y -= e.y;
-          ai.z -= e.z;
-          ai.w -= e.w;
-          aj.y += e.y;
-          aj.z += e.z;
-          aj.w += e.w;
-          w.acc[pi] = ai;
-          w.acc[pj] = aj;
+        // active pairs in table order (lane order within the chunk), one at a
+        // time, so every sphere receives its self terms in that order: the
+        // active lanes stage their pairs in lane order and lane 0 applies
+        // them (one divergent region and two warp barriers per round, not per
+        // pair).  (Measured and slower: each pair's own lane applying it,
+        // behind a warp barrier per pair; the owners of the spheres
+        // accumulating in registers from shuffled pairs; updating all at once
+        // when no two active pairs of a chunk share a sphere; listing the kept
+        // cluster pairs of all chunks first and expanding them together.)
+        const unsigned am = __ballot_sync(FULL_MASK, act);
+        if (act) {
+          selfsum += pen;
+          w.stage[__popc(am & ((1u << lane) - 1u))] = make_float4(__int_as_float(i | (j << 16)), ux, uy, uz);
         }
+        __syncwarp();
+        if (lane == 0) {
+          const int na = __popc(am);
+          for (int k = 0; k < na; ++k) {
+            const float4 e = w.stage[k];
+            const int pi = __float_as_int(e.x) & 0xffff, pj = __float_as_int(e.x) >> 16;
+            float4 ai = w.acc[pi], aj = w.acc[pj];  // both loads first (a pair with i == j has u = 0)
+            ai.y -= e.y;
+            ai.z -= e.z;
+            ai.w -= e.w;
+            aj.y += e.y;
+            aj.z += e.z;
+            aj.w += e.w;
+            w.acc[pi] = ai;
+            w.acc[pj] = aj;
+          }
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
+    __syncwarp();  // w.kept is rewritten by the next KEPT_CAP
   }
   __syncwarp();
   (void)S;
