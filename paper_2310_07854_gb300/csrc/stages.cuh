@@ -739,11 +739,13 @@ __device__ __forceinline__ void env_bits_direct(const SceneSm& m, int obase, uns
 // pair (a, b) whose spheres are apart by d_ab - rho_a - rho_b >= eta_s (+ a
 // rounding margin) holds no pair with |c_i - c_j| < r_i + r_j + eta_s, since
 // |c_i - c_j| >= d_ab - (rho_a - r_i) - (rho_b - r_j): its pairs are skipped.
-// (A NaN anywhere keeps the cluster pair.)  The kept cluster pairs of each
-// 32 are expanded into their pairs through a warp prefix sum of their pair
-// counts (lane t of a chunk finds its cluster pair by binary search), and
-// the pairs are tested in table order; each active pair's gradient is added
-// to its two spheres in that order, one pair at a time.
+// (A NaN anywhere keeps the cluster pair.)  The cluster pairs are tested
+// KEPT_CAP at a time and the kept ones listed in table order; 32 listed
+// cluster pairs at a time are expanded into their pairs through a warp
+// prefix sum of their pair counts (lane t of a round finds its cluster pair
+// by binary search), and the pairs are tested in table order; each active
+// pair's gradient is added to its two spheres in that order, one pair at a
+// time.
 __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m, const CollWarp& w,
                                             int S, float w_s, int lane) {
   const int NC = rb.n_cl[0], NG = m.self_meta[0];
@@ -835,15 +837,14 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
             uz = dz * inv;
           }
         }
-        // active pairs in table order (lane order within the chunk), one at a
-        // time, so every sphere receives its self terms in that order: the
+        // active pairs in table order (lane order within the round), one at
+        // a time, so every sphere receives its self terms in that order: the
         // active lanes stage their pairs in lane order and lane 0 applies
-        // them (one divergent region and two warp barriers per round, not per
-        // pair).  (Measured and slower: each pair's own lane applying it,
-        // behind a warp barrier per pair; the owners of the spheres
-        // accumulating in registers from shuffled pairs; updating all at once
-        // when no two active pairs of a chunk share a sphere; listing the kept
-        // cluster pairs of all chunks first and expanding them together.)
+        // them (one divergent region and two warp barriers per round, not
+        // per pair).  (Measured and slower: each pair's own lane applying
+        // it, behind a warp barrier per pair; the owners of the spheres
+        // accumulating in registers from shuffled pairs; updating all at
+        // once when no two active pairs of a round share a sphere.)
         const unsigned am = __ballot_sync(FULL_MASK, act);
         if (act) {
           selfsum += pen;
