@@ -421,14 +421,16 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
 // order and 16-byte alignment, thresholds without eta_s), and a block
 // whose robot carries such tables copies them (load_robot_self) instead of
 // building them, after checking that they were made for the robot's
-// current contents (a hash of its arrays, as the scene grid is checked).
+// current contents (a hash of its arrays, as the scene grid is checked) and
+// are intact (a hash of the image body).
 // A threshold (r_i + r_j) + eta_s is rounded as load_self rounds it, so
 // copied and built tables are the same bytes.
 constexpr uint32_t TABLES_MAGIC = 0x56525442u;
 
 struct TablesHeader {
   uint32_t magic, J, S, NP, hash, NG;
-  uint32_t pad[10];  // 64 bytes
+  uint32_t body_words, body_hash;  // the 32-bit words after the header, and their hash
+  uint32_t pad[8];  // 64 bytes
 };
 static_assert(sizeof(TablesHeader) == 64, "the arrays after the header stay 16-byte aligned");
 
@@ -465,6 +467,13 @@ __device__ __forceinline__ uint32_t robot_hash_part(const RobotArgs& r, int tid,
   return s;
 }
 
+// Hash of words [0, nw) of a table image's body, as the robot hash.
+__device__ __forceinline__ uint32_t body_hash_part(const uint32_t* body, uint32_t nw, int tid, int stride) {
+  uint32_t s = 0;
+  for (uint32_t i = tid; i < nw; i += stride) s += fmix32(__ldcg(body + i) ^ fmix32(i * 0x85ebca6bu + 0x2545f491u));
+  return s;
+}
+
 // 16-byte granules of an array (its padding to 16 bytes included).
 __device__ __forceinline__ void copy_granules(void* dst, const void* src, size_t bytes) {
   const int n = (int)((bytes + 15) / 16);
@@ -478,18 +487,28 @@ __device__ __forceinline__ void copy_granules(void* dst, const void* src, size_t
 // Ends with the block synchronised.
 __device__ inline void load_robot_self(const RobotArgs& r, const RobotSm& rb, const SceneSm& m,
                                        const SelfScratch& t, float eta_s) {
-  __shared__ uint32_t s_hash;
+  __shared__ uint32_t s_hash, s_body;
   __shared__ int s_ok;
   const TablesHeader* h = static_cast<const TablesHeader*>(r.tables);
   bool ok = false;
   if (h) {  // uniform over the block
-    if (threadIdx.x == 0) s_hash = 0u;
+    Bump b0(nullptr);
+    RobotImage im0;
+    carve_image(b0, r.J, r.S, r.NP, im0);
+    const uint32_t nw = (uint32_t)((b0.bytes() - sizeof(TablesHeader)) / 4);
+    if (threadIdx.x == 0) {
+      s_hash = 0u;
+      s_body = 0u;
+    }
     __syncthreads();
     atomicAdd(&s_hash, robot_hash_part(r, threadIdx.x, blockDim.x));
+    const bool sized = __ldcg(&h->body_words) == nw;  // the body read below stays inside the image
+    if (sized) atomicAdd(&s_body, body_hash_part(reinterpret_cast<const uint32_t*>(h + 1), nw, threadIdx.x,
+                                                 blockDim.x));
     __syncthreads();
     if (threadIdx.x == 0)
-      s_ok = h->magic == TABLES_MAGIC && h->J == (uint32_t)r.J && h->S == (uint32_t)r.S &&
-             h->NP == (uint32_t)r.NP && h->hash == s_hash;
+      s_ok = sized && h->magic == TABLES_MAGIC && h->J == (uint32_t)r.J && h->S == (uint32_t)r.S &&
+             h->NP == (uint32_t)r.NP && h->hash == s_hash && h->body_hash == s_body;
     __syncthreads();
     ok = s_ok != 0;
   }

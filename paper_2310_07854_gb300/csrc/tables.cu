@@ -59,9 +59,18 @@ __global__ void __launch_bounds__(TB_THREADS) robot_tables_kernel(RobotArgs r, u
   store_granules(im.cp, s.sm.cp, NG * sizeof(uint16_t));
   store_granules(im.cp_start, s.sm.cp_start, (NG + 1) * sizeof(uint16_t));
   __syncthreads();
+  const uint32_t nw = (uint32_t)((g.bytes() - sizeof(TablesHeader)) / 4);
+  __shared__ uint32_t s_body;
+  if (threadIdx.x == 0) s_body = 0u;
+  __syncthreads();
+  atomicAdd(&s_body, body_hash_part(reinterpret_cast<const uint32_t*>(im.h + 1), nw, threadIdx.x, blockDim.x));
+  __threadfence();  // the arrays before the header that validates them, for every observer
+  __syncthreads();
   if (threadIdx.x == 0) {
     TablesHeader h;
-    for (int i = 0; i < 10; ++i) h.pad[i] = 0u;
+    for (int i = 0; i < 8; ++i) h.pad[i] = 0u;
+    h.body_words = nw;
+    h.body_hash = s_body;
     h.magic = TABLES_MAGIC;
     h.J = (uint32_t)J;
     h.S = (uint32_t)S;

@@ -185,6 +185,9 @@ class Evaluator:
         evs = [self, self._twin(n)]
         qd = [torch.empty((n, J), dtype=torch.float32, device=dev) for _ in range(2)]
         sc, si, so = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        cur = torch.cuda.current_stream()
+        for st in (sc, si, so):  # the evaluators' tables and buffers were made on the current stream
+            st.wait_stream(cur)
         graphs = []
         for b in range(2):
             with torch.cuda.stream(sc):

@@ -106,3 +106,26 @@ def test_stale_tables_are_ignored():
     torch.cuda.synchronize()
     for x, y in zip((cost, dist, jg), want2):
         assert torch.equal(x, y)
+
+
+def test_damaged_tables_are_ignored():
+    """A tables buffer whose body was overwritten after the build (the
+    header left alone) fails the body hash, and the launch builds its own."""
+    import torch
+    w = synth.make_workload("sweep_1024")
+    n, q, table = w.n, to_dev(w.q), F.FP32_TABLE
+    want = _run(w.robot, w.scene, w.params, q, n, table, False)
+    rd = B.DeviceRobot(w.robot)
+    body = rd.tables[64:]
+    body[: body.numel() // 2] = 0xFF  # cluster and pair tables out of range
+    sd = B.DeviceScene(w.scene)
+    sd.build_grid(float(np.max(w.robot.sphere_local[:, 3])), w.params.eta, 32)
+    S, J = w.robot.n_spheres, w.robot.n_joints
+    cost = torch.empty(n, device="cuda")
+    dist = B.alloc_packed(n, S, table.dist)
+    jg = B.alloc_packed(n, J, table.jgrad)
+    B.vapr_cost_grad(rd, sd, w.params, q, n, table, None, cost, dist, jg, B.alloc_workspace(rd, n, table))
+    torch.cuda.synchronize()
+    for x, y in zip((cost, dist, jg), want):
+        assert torch.equal(x, y)
+    assert B.vapr_device_error() == 0
