@@ -127,9 +127,9 @@ typedef struct {
  * that takes each block about 10 us for an arm with 832 pairs; with
  * robot->tables set, the blocks copy tables built once instead.  Each
  * launch checks on the device that the tables were built for the robot's
- * current joint, sphere, link and pair words (a hash) and are intact (a hash
- * of the tables themselves), and otherwise builds its own, so stale or
- * damaged tables cost speed, never correctness.  The tables do
+ * current joint, sphere, link and pair words (a hash) and are intact (a
+ * checksum of the tables themselves), and otherwise builds its own, so stale
+ * or damaged tables cost speed, never correctness.  The tables do
  * not depend on the cost parameters. */
 /* bytes of the tables of `robot` (0 when the robot is invalid) */
 size_t vapr_robot_tables_bytes(const vapr_robot* robot);

@@ -422,7 +422,7 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
 // whose robot carries such tables copies them (load_robot_self) instead of
 // building them, after checking that they were made for the robot's
 // current contents (a hash of its arrays, as the scene grid is checked) and
-// are intact (a hash of the image body).
+// are intact (a checksum of the image body).
 // A threshold (r_i + r_j) + eta_s is rounded as load_self rounds it, so
 // copied and built tables are the same bytes.
 constexpr uint32_t TABLES_MAGIC = 0x56525442u;
@@ -467,10 +467,12 @@ __device__ __forceinline__ uint32_t robot_hash_part(const RobotArgs& r, int tid,
   return s;
 }
 
-// Hash of words [0, nw) of a table image's body, as the robot hash.
+// Checksum of words [0, nw) of a table image's body: the sum of word i
+// times 2i + 1 (mod 2^32), which any change of a single word alters (odd
+// factors are invertible), at one multiply-add per word.
 __device__ __forceinline__ uint32_t body_hash_part(const uint32_t* body, uint32_t nw, int tid, int stride) {
   uint32_t s = 0;
-  for (uint32_t i = tid; i < nw; i += stride) s += fmix32(__ldcg(body + i) ^ fmix32(i * 0x85ebca6bu + 0x2545f491u));
+  for (uint32_t i = tid; i < nw; i += stride) s += __ldcg(body + i) * (2u * i + 1u);
   return s;
 }
 
