@@ -13,8 +13,8 @@
 // loading them would.
 //
 // A block of FU_WARPS warps takes a contiguous range of mini-tiles of
-// FU_MT = 8 configurations, which its warps draw one at a time from a block
-// counter.  A warp runs its mini-tile's joint chains (lanes 0..7, one
+// FU_MT = 4 configurations, which its warps draw one at a time from a block
+// counter.  A warp runs its mini-tile's joint chains (lanes 0..3, one
 // configuration each) into its own transform rows in shared memory, then
 // takes the configurations one by one: it computes the sphere centres from
 // the transforms (lanes over spheres), runs the collision stage's
@@ -27,13 +27,18 @@
 // same operations, so J is the staged path's bit for bit too (with the
 // transforms recomputed there, not stored).  A first version shared
 // 32-configuration tiles across the block, behind block barriers: warps
-// idled at each tile's end, 0.61 of the staged speed at 2^20.
+// idled at each tile's end, 0.61 of the staged speed at 2^20.  Mini-tiles
+// of 8 configurations (twice the transform rows, and a longer serial chain
+// phase per warp) ran at 0.71 of the staged speed at 32,768 configurations,
+// against 0.86 with 4.  Splitting each chain over three
+// lanes (one transform row each) gained nothing: the chains are a small
+// part of a mini-tile's time next to its sphere tests.
 #include "stages.cuh"
 
 namespace vapr {
 
 constexpr int FU_WARPS = 8;
-constexpr int FU_MT = 8;  // configurations per mini-tile (a warp's chains)
+constexpr int FU_MT = 4;  // configurations per mini-tile (a warp's chains)
 
 struct FusedArgs {
   RobotArgs r;
