@@ -90,7 +90,7 @@ __host__ __device__ inline void carve_batch(Bump& b, const BatchArgs& a, RobotSm
   const int tstride = (3 * a.maxJ) | 1, kstride = (2 * a.maxJ) | 1;
   sU = b.take<float4>((size_t)a.tile * (tstride > kstride ? tstride : kstride));  // T, then K
   sQ = b.take<float>((size_t)a.tile * a.maxJ);
-  carve_self_scratch(t, a.maxNP, cluster_bound(a.maxS, a.maxJ), scratch);
+  carve_self_scratch(t, a.maxNP, cluster_bound(a.maxS, a.maxJ), a.maxS, scratch);
   if (t.off > b.off) b.off = t.off;
   sItem = b.take<int>(4);
 }

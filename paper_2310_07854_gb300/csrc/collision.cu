@@ -21,7 +21,7 @@
 // them alone, in the same order.
 //
 // Self pairs: the block groups the pair table by cluster pair (runs of up to
-// three spheres of one link, load_self), or copies the robot's prebuilt
+// CL spheres of one link, load_self), or copies the robot's prebuilt
 // tables (load_robot_self: a hash-checked copy instead of about 10 us of
 // building per block); per configuration, cluster pairs whose bounding
 // spheres are apart are skipped and the pairs of the others tested in
@@ -30,9 +30,10 @@
 // Determinism: every sphere adds its terms in cuboid order in one register,
 // and a skipped pair would have added exactly zero, so the result of a
 // configuration does not depend on the batch it is in or on which pairs the
-// bounding test lets through.  Active self pairs are applied one at a time
-// in table order; which lane sums a pair's penetration follows from the
-// configuration's own kept cluster pairs.
+// bounding test lets through.  The self terms' gradients are summed in
+// fixed point (integer sums, the same in any order); which lane sums a
+// pair's penetration follows from the configuration's own kept cluster
+// pairs.
 #include <map>
 #include <mutex>
 
@@ -84,11 +85,13 @@ __host__ __device__ inline void carve_coll(Bump& b, const RobotArgs& r, int O, R
     carve_coll_warp(b, r.S, r.J, cw);
     if (w == mine) w_mine = cw;
   }
-  carve_self_scratch(t, r.NP, cluster_bound(r.S, r.J), scratch);
+  carve_self_scratch(t, r.NP, cluster_bound(r.S, r.J), r.S, scratch);
   if (t.off > b.off) b.off = t.off;
 }
 
-template <bool MASKED>
+// F32: P, D and G are float32 (the loop body without the other formats'
+// code, which keeps it within the instruction cache).
+template <bool MASKED, bool F32>
 __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs a) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
       if (cn < c_end && 128 * lane < a.pos.stride)
         asm volatile("prefetch.global.L1 [%0];" ::"l"(a.pos.ptr + cn * a.pos.stride + 128 * lane));
     };
-    collision_config<false, MASKED>(a.r, a.sc.O, rb, sm, w,
+    collision_config<false, MASKED, F32>(a.r, a.sc.O, rb, sm, w,
                                     reinterpret_cast<const uint32_t*>(a.pos.ptr + c * a.pos.stride),
                                     a.pos.f, a.dist.f, a.grad.f, a.eta, a.w_c, a.w_s, out, lane,
                                     MASKED ? a.est + c * a.r.S : nullptr, a.margin, grid, cells, prefetch_next);
@@ -227,8 +230,11 @@ cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc, const vapr
   SelfScratch scratch;
   carve_coll(b, r, sc.O, rb, sm, w, 0, scratch);
   const size_t smem = b.bytes();
-  const void* fn = est ? (const void*)collision_kernel<true> : (const void*)collision_kernel<false>;
-  const int per_sm = blocks_per_sm(fn, COLL_WARPS * 32, smem);
+  const bool f32 = pos.f.kind == KIND_F32 && (!dist.ptr || dist.f.kind == KIND_F32) &&
+                   (!grad.ptr || grad.f.kind == KIND_F32);
+  auto kernel = est ? (f32 ? collision_kernel<true, true> : collision_kernel<true, false>)
+                    : (f32 ? collision_kernel<false, true> : collision_kernel<false, false>);
+  const int per_sm = blocks_per_sm((const void*)kernel, COLL_WARPS * 32, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   const int64_t blocks = (n + COLL_WARPS - 1) / COLL_WARPS;
   const int grid = (int)(blocks < (int64_t)sm_count() * per_sm ? blocks : (int64_t)sm_count() * per_sm);
@@ -236,8 +242,7 @@ cudaError_t launch_collision(const RobotArgs& r, const SceneArgs& sc, const vapr
   std::lock_guard<std::mutex> hold(P.mu);  // slot choice, launch and its event together
   cudaEvent_t rec;
   a.slot = sched_slot(P, st, n, &rec);
-  cudaError_t e = est ? launch_after(overlap, collision_kernel<true>, grid, COLL_WARPS * 32, smem, st, a)
-                      : launch_after(overlap, collision_kernel<false>, grid, COLL_WARPS * 32, smem, st, a);
+  cudaError_t e = launch_after(overlap, kernel, grid, COLL_WARPS * 32, smem, st, a);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess && rec) return cudaEventRecord(rec, st);
   return e;

@@ -79,7 +79,7 @@ __host__ __device__ inline void carve_fused(Bump& b, const FusedArgs& a, RobotSm
       f_mine = fw;
     }
   }
-  carve_self_scratch(t, r.NP, cluster_bound(r.S, r.J), scratch);  // over the warps' sets (built first)
+  carve_self_scratch(t, r.NP, cluster_bound(r.S, r.J), r.S, scratch);  // over the warps' sets (built first)
   if (t.off > b.off) b.off = t.off;
   for (int w = 0; w < FU_WARPS; ++w) {  // (after the scratch: written once the tables are built)
     float4* T = b.take<float4>((size_t)FU_MT * a.tstride);

@@ -41,28 +41,43 @@ static_assert(sizeof(GridHeader) <= GRID_HEADER_BYTES, "grid header");
 
 __host__ __device__ constexpr int grid_words(int O) { return 2 * (((O > 0 ? O : 1) + 63) / 64); }
 
-// MurmurHash3's 32-bit finaliser (Appleby), a bijective bit mixer.
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
+// Term of word w at position i of a hashed sequence: w xor a Weyl-sequence
+// key of i, times an odd constant, then an xorshift, so each step (and the
+// term, for a fixed i) is a bijection of w: changing any one word changes
+// the sum of the terms.  Three integer operations and an index multiply-add
+// per word.
+__device__ __forceinline__ uint32_t hash_word(uint32_t w, uint32_t i) {
+  const uint32_t h = (w ^ (i * 0x9e3779b9u + 0x7f4a7c15u)) * 0x85ebca6bu;
+  return h ^ (h >> 15);
 }
 
-// One thread's share of the scene hash: the sum (mod 2^32) over the words
-// i = tid, tid + stride, ... of the 15 O pose and half-extent words of
-// mix(word, i).  The sum does not depend on how the words are split, so a
-// block adds its threads' shares with atomics.
-__device__ __forceinline__ uint32_t scene_hash_part(const SceneArgs& sc, int tid, int stride) {
+// One thread's share (words tid, tid + stride, ... in 16-byte groups when
+// VEC) of the sum of hash_word(p[k], base + k) over k < n.  VEC: p is
+// 16-byte aligned.  The sum does not depend on how the words are split, so
+// a block adds its threads' shares with atomics.
+template <bool VEC>
+__device__ __forceinline__ uint32_t hash_words(const uint32_t* p, int n, uint32_t base, int tid, int stride) {
   uint32_t s = 0;
-  const int np = 12 * sc.O, nw = 15 * sc.O;
-  for (int i = tid; i < nw; i += stride) {
-    const uint32_t w = i < np ? __float_as_uint(sc.pose[i]) : __float_as_uint(sc.half[i - np]);
-    s += fmix32(w ^ fmix32((uint32_t)i * 0x9e3779b9u + 0x7f4a7c15u));
+  int k0 = 0;
+  if constexpr (VEC) {
+    const int nq = n >> 2;
+    for (int q = tid; q < nq; q += stride) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + q);
+      const uint32_t i = base + 4u * (uint32_t)q;
+      s += hash_word(v.x, i) + hash_word(v.y, i + 1u) + hash_word(v.z, i + 2u) + hash_word(v.w, i + 3u);
+    }
+    k0 = 4 * nq;
   }
+  for (int k = k0 + tid; k < n; k += stride) s += hash_word(__ldg(p + k), base + (uint32_t)k);
   return s;
+}
+
+// One thread's share of the scene hash: the sum (mod 2^32) of hash_word
+// over the 12 O pose words, then the 3 O half-extent words.
+__device__ __forceinline__ uint32_t scene_hash_part(const SceneArgs& sc, int tid, int stride) {
+  const int np = 12 * sc.O;
+  return hash_words<true>(reinterpret_cast<const uint32_t*>(sc.pose), np, 0u, tid, stride) +
+         hash_words<false>(reinterpret_cast<const uint32_t*>(sc.half), 3 * sc.O, (uint32_t)np, tid, stride);
 }
 
 // Bounding radius of cuboid o's test as the collision stage computes it

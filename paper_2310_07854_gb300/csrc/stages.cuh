@@ -53,7 +53,7 @@ struct RobotSm {
   int* cl_start;  // [NC+1] cluster c = spheres order[cl_start[c] .. cl_start[c+1])
   int* cl_of;     // [S] cluster of each sphere
   int* cl_sph;    // [NC] cluster c's spheres: s0 | s1 << 8 | s2 << 16 | count << 24
-  int* n_cl;      // [1] NC
+  int* n_cl;      // [2] NC, and the exponent e of the self terms' fixed point (self_pairs)
 };
 
 __host__ __device__ inline void carve_robot(Bump& b, int J, int S, RobotSm& r) {
@@ -65,7 +65,7 @@ __host__ __device__ inline void carve_robot(Bump& b, int J, int S, RobotSm& r) {
   r.cl_start = b.take<int>(cluster_bound(S, J) + 1);
   r.cl_of = b.take<int>(S);
   r.cl_sph = b.take<int>(cluster_bound(S, J));
-  r.n_cl = b.take<int>(1);
+  r.n_cl = b.take<int>(2);
 }
 
 // Block-cooperative (every thread calls it); the caller synchronises the
@@ -249,7 +249,7 @@ struct SceneSm {
   float4* cubH;  // [O]: (half extents, unused)
   float4* cubC;  // [O]: (centre, bounding radius + eta + SLACK)
   // self pairs, grouped by cluster pair (load_self)
-  uint2* pairs;         // [NP]: (i | j << 16, bits of r_i + r_j + eta_s), cluster-pair major
+  uint32_t* pairs;      // [NP]: i | j << 16, cluster-pair major (threshold (r_i + r_j) + eta_s from the radii)
   uint16_t* cp;         // [NG]: cluster pair a | b << 8 (a <= b), in increasing a * NC + b
   uint16_t* cp_start;   // [NG+1]: its pairs are pairs[cp_start[g] .. cp_start[g+1])
   int* self_meta;       // [2]: NG, bits of eta_s
@@ -265,7 +265,7 @@ __host__ __device__ inline void carve_scene(Bump& b, int O, int NP, int NCB, Sce
   s.cubH = b.take<float4>(O);
   s.cubC = b.take<float4>(O);
   const int NG = pair_groups_bound(NP, NCB);
-  s.pairs = b.take<uint2>(NP);
+  s.pairs = b.take<uint32_t>(NP);
   s.cp = b.take<uint16_t>(NG);
   s.cp_start = b.take<uint16_t>(NG + 1);
   s.self_meta = b.take<int>(2);
@@ -279,10 +279,12 @@ struct SelfScratch {
   uint16_t* g_of_key;  // [NC^2]
   uint32_t* keymap;    // [NC^2 / 32] keys that occur
   int* keybase;        // [NC^2 / 32] keys that occur in earlier keymap words
+  int* deg;            // [S] pairs naming each sphere (a pair (i, i) twice)
 };
 
-__host__ __device__ inline void carve_self_scratch(Bump& b, int NP, int NCB, SelfScratch& t) {
+__host__ __device__ inline void carve_self_scratch(Bump& b, int NP, int NCB, int S, SelfScratch& t) {
   const int keys = NP > 0 ? NCB * NCB : 0;
+  t.deg = b.take<int>(S);
   t.word = b.take<uint32_t>(NP);
   t.cursor = b.take<int>(pair_groups_bound(NP, NCB));
   t.g_of_key = b.take<uint16_t>(keys);
@@ -333,11 +335,15 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
       m.self_meta[0] = 0;
       m.self_meta[1] = (int)__float_as_uint(eta_s);
       m.cp_start[0] = 0;
+      rb.n_cl[1] = 30;
     }
     __syncthreads();
     return;
   }
+  __shared__ int s_maxdeg;
   for (int k = threadIdx.x; k < kw; k += blockDim.x) t.keymap[k] = 0u;
+  for (int k = threadIdx.x; k < r.S; k += blockDim.x) t.deg[k] = 0;
+  if (threadIdx.x == 0) s_maxdeg = 1;
   __syncthreads();
   for (int p = threadIdx.x; p < NP; p += blockDim.x) {
     const int i = clampi(r.pairs[2 * p], 0, r.S - 1), j = clampi(r.pairs[2 * p + 1], 0, r.S - 1);
@@ -345,8 +351,16 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
     const int key = a <= b ? a * NC + b : b * NC + a;
     t.word[p] = (uint32_t)i | ((uint32_t)j << 7) | ((uint32_t)key << 14);
     atomicOr(&t.keymap[key >> 5], 1u << (key & 31));
+    atomicAdd(&t.deg[i], 1);
+    atomicAdd(&t.deg[j], 1);
   }
   __syncthreads();
+  for (int k = threadIdx.x; k < r.S; k += blockDim.x) atomicMax(&s_maxdeg, t.deg[k]);
+  __syncthreads();
+  // The self terms' fixed point (self_pairs): a sphere's sum of at most
+  // maxdeg unit-vector components times 2^e, e = 30 - floor(log2 maxdeg),
+  // stays below 2^31 (maxdeg 2^(30-e+1) - 1 at most: 2^31 - 2^e).
+  if (threadIdx.x == 0) rb.n_cl[1] = __clz(s_maxdeg) - 1;
   if (warp == 0) {  // keys occurring in earlier words
     int base = 0;
     for (int k0 = 0; k0 < kw; k0 += 32) {
@@ -401,9 +415,7 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
       const unsigned same = __match_any_sync(FULL_MASK, g);
       if (p < NP) {
         const int i = (int)(wd & 0x7fu), j = (int)((wd >> 7) & 0x7fu);
-        m.pairs[t.cursor[g] + __popc(same & ((1u << lane) - 1u))] =
-            make_uint2((uint32_t)i | ((uint32_t)j << 16),
-                       __float_as_uint(rb.sph[i].w + rb.sph[j].w + eta_s));
+        m.pairs[t.cursor[g] + __popc(same & ((1u << lane) - 1u))] = (uint32_t)i | ((uint32_t)j << 16);
       }
       __syncwarp();
       if (p < NP && lane == __ffs(same) - 1) t.cursor[g] += __popc(same);
@@ -415,17 +427,14 @@ __device__ inline void load_self(const RobotArgs& r, const RobotSm& rb, const Sc
 
 // ------------------------------------------------- prebuilt robot tables
 // What load_robot, load_clusters and load_self build in shared memory
-// depends on the robot alone, but for the self-pair thresholds
-// r_i + r_j + eta_s: vapr_robot_tables_build stores it once in global
-// memory (RobotImage: a header, then the shared-memory arrays in the same
-// order and 16-byte alignment, thresholds without eta_s), and a block
-// whose robot carries such tables copies them (load_robot_self) instead of
-// building them, after checking that they were made for the robot's
-// current contents (a hash of its arrays, as the scene grid is checked) and
-// are intact (a checksum of the image body).
-// A threshold (r_i + r_j) + eta_s is rounded as load_self rounds it, so
-// copied and built tables are the same bytes.
-constexpr uint32_t TABLES_MAGIC = 0x56525442u;
+// depends on the robot alone: vapr_robot_tables_build stores it once in
+// global memory (RobotImage: a header, then the shared-memory arrays in the
+// same order and 16-byte alignment), and a block whose robot carries such
+// tables copies them (load_robot_self) instead of building them, after
+// checking that they were made for the robot's current contents (a hash of
+// its arrays, as the scene grid is checked) and are intact (a checksum of
+// the image body).  Copied and built tables are the same bytes.
+constexpr uint32_t TABLES_MAGIC = 0x56525443u;
 
 struct TablesHeader {
   uint32_t magic, J, S, NP, hash, NG;
@@ -437,7 +446,7 @@ static_assert(sizeof(TablesHeader) == 64, "the arrays after the header stay 16-b
 struct RobotImage {
   TablesHeader* h;
   RobotSm rb;
-  uint2* pairs;
+  uint32_t* pairs;
   uint16_t* cp;
   uint16_t* cp_start;
 };
@@ -446,33 +455,37 @@ __host__ __device__ inline void carve_image(Bump& b, int J, int S, int NP, Robot
   im.h = b.take<TablesHeader>(1);
   carve_robot(b, J, S, im.rb);
   const int NG = pair_groups_bound(NP, cluster_bound(S, J));
-  im.pairs = b.take<uint2>(NP);
+  im.pairs = b.take<uint32_t>(NP);
   im.cp = b.take<uint16_t>(NG);
   im.cp_start = b.take<uint16_t>(NG + 1);
 }
 
-// Hash of the robot's arrays (and sizes): the sum over words of
-// mix(word, i), as the scene grid's hash.
+// Hash of the robot's arrays (and sizes): the sum of hash_word over the
+// joint, sphere, link and pair words in that order, as the scene grid's
+// hash (all four arrays are 16-byte aligned).
 __device__ __forceinline__ uint32_t robot_hash_part(const RobotArgs& r, int tid, int stride) {
-  uint32_t s = 0;
-  const int n0 = 12 * r.J, n1 = n0 + 4 * r.S, n2 = n1 + r.S, nw = n2 + 2 * r.NP;
-  for (int i = tid; i < nw; i += stride) {
-    const uint32_t w = i < n0   ? __float_as_uint(r.joint_fixed[i])
-                       : i < n1 ? __float_as_uint(r.sphere_local[i - n0])
-                       : i < n2 ? (uint32_t)r.sphere_link[i - n1]
-                                : (uint32_t)r.pairs[i - n2];
-    s += fmix32(w ^ fmix32((uint32_t)i * 0x9e3779b9u + 0x7f4a7c15u));
-  }
-  if (tid == 0) s += fmix32((uint32_t)r.J * 0x01000193u ^ (uint32_t)r.S << 8 ^ (uint32_t)r.NP << 16);
+  const int n0 = 12 * r.J, n1 = 4 * r.S, n2 = r.S, n3 = 2 * r.NP;
+  uint32_t s = hash_words<true>(reinterpret_cast<const uint32_t*>(r.joint_fixed), n0, 0u, tid, stride) +
+               hash_words<true>(reinterpret_cast<const uint32_t*>(r.sphere_local), n1, (uint32_t)n0, tid, stride) +
+               hash_words<true>(reinterpret_cast<const uint32_t*>(r.sphere_link), n2, (uint32_t)(n0 + n1), tid,
+                                stride);
+  if (n3 > 0)
+    s += hash_words<true>(reinterpret_cast<const uint32_t*>(r.pairs), n3, (uint32_t)(n0 + n1 + n2), tid, stride);
+  if (tid == 0) s += hash_word((uint32_t)r.J ^ (uint32_t)r.S << 8 ^ (uint32_t)r.NP << 16, 0xffffffffu);
   return s;
 }
 
-// Checksum of words [0, nw) of a table image's body: the sum of word i
-// times 2i + 1 (mod 2^32), which any change of a single word alters (odd
-// factors are invertible), at one multiply-add per word.
+// Checksum of words [0, nw) of a table image's body (16-byte aligned, nw a
+// multiple of 4): the sum of word i times 2i + 1 (mod 2^32), which any
+// change of a single word alters (odd factors are invertible), at one
+// multiply-add per word, four words per load.
 __device__ __forceinline__ uint32_t body_hash_part(const uint32_t* body, uint32_t nw, int tid, int stride) {
   uint32_t s = 0;
-  for (uint32_t i = tid; i < nw; i += stride) s += __ldcg(body + i) * (2u * i + 1u);
+  for (uint32_t q = tid; q < nw / 4u; q += stride) {
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(body) + q);
+    const uint32_t i = 8u * q + 1u;  // 2 (4q) + 1
+    s += v.x * i + v.y * (i + 2u) + v.z * (i + 4u) + v.w * (i + 6u);
+  }
   return s;
 }
 
@@ -533,13 +546,10 @@ __device__ inline void load_robot_self(const RobotArgs& r, const RobotSm& rb, co
   copy_granules(rb.cl_start, im.rb.cl_start, (NCB + 1) * sizeof(int));
   copy_granules(rb.cl_of, im.rb.cl_of, S * sizeof(int));
   copy_granules(rb.cl_sph, im.rb.cl_sph, NCB * sizeof(int));
-  copy_granules(rb.n_cl, im.rb.n_cl, sizeof(int));
+  copy_granules(rb.n_cl, im.rb.n_cl, 2 * sizeof(int));
   copy_granules(m.cp, im.cp, NG * sizeof(uint16_t));
   copy_granules(m.cp_start, im.cp_start, (NG + 1) * sizeof(uint16_t));
-  for (int p = threadIdx.x; p < r.NP; p += blockDim.x) {
-    const uint2 pr = __ldg(im.pairs + p);
-    m.pairs[p] = make_uint2(pr.x, __float_as_uint(__uint_as_float(pr.y) + eta_s));
-  }
+  copy_granules(m.pairs, im.pairs, r.NP * sizeof(uint32_t));
   if (threadIdx.x == 0) {
     m.self_meta[0] = NG;
     m.self_meta[1] = (int)__float_as_uint(eta_s);
@@ -554,7 +564,7 @@ struct CollWarp {
   float4* P;       // [S] (x, y, z, r)
   float4* acc;     // [S] (D, gx, gy, gz)
   float4* cls;     // [NC] cluster bounding spheres of this configuration (centre, radius)
-  float4* stage;   // [32] a round's active self pairs (i | j << 16, u), in lane order
+  int4* gi;        // [S] self-term gradient sums of this configuration, fixed point 2^-e (.w unused)
   uint16_t* kept;  // [KEPT_CAP] kept cluster pairs, in table order
 };
 
@@ -562,7 +572,7 @@ __host__ __device__ inline void carve_coll_warp(Bump& b, int S, int J, CollWarp&
   w.P = b.take<float4>(S);
   w.acc = b.take<float4>(S);
   w.cls = b.take<float4>(cluster_bound(S, J));
-  w.stage = b.take<float4>(32);
+  w.gi = b.take<int4>(S);
   w.kept = b.take<uint16_t>(KEPT_CAP);
 }
 
@@ -636,12 +646,13 @@ struct CollOut {
 
 // Decodes the sphere centres of one packed P row into P[s].xyz (one word per
 // lane; .w is left alone).  COHERENT: loads that see writes made earlier in
-// the same kernel.
-template <bool COHERENT>
+// the same kernel.  F32: the row is float32 (no other format's code is
+// compiled in: a smaller loop body for the instruction cache).
+template <bool COHERENT, bool F32 = false>
 __device__ __forceinline__ void load_centres(const uint32_t* prow, const DevFmt& fP, int S, float4* P,
                                              int lane) {
   const int nv = 3 * S;
-  if (fP.kind == KIND_F32) {  // float32: lane s takes sphere s's three words
+  if (F32 || fP.kind == KIND_F32) {  // float32: lane s takes sphere s's three words
     for (int s = lane; s < S; s += 32) {
       const uint32_t* r = prow + 3 * s;
       float* d = reinterpret_cast<float*>(P + s);
@@ -651,7 +662,7 @@ __device__ __forceinline__ void load_centres(const uint32_t* prow, const DevFmt&
     }
     return;
   }
-  dispatch_kind(fP.kind, [&](auto kc) {
+  if constexpr (!F32) dispatch_kind(fP.kind, [&](auto kc) {
     constexpr int K = decltype(kc)::value;
     const int kw = per_word<K>(fP);
     const int nw = (nv + kw - 1) / kw;
@@ -666,7 +677,8 @@ __device__ __forceinline__ void load_centres(const uint32_t* prow, const DevFmt&
 }
 
 // Cost (w_c sum_s acc[s].x + extra) and the packed D row (acc.x) of one
-// configuration, one word per lane.
+// configuration, one word per lane.  F32: D is float32.
+template <bool F32 = false>
 __device__ __forceinline__ void coll_cost_dist(const CollWarp& w, int S, const DevFmt& fD, float w_c, float extra,
                                                const CollOut& out, int lane) {
   float local = 0.f;
@@ -675,7 +687,9 @@ __device__ __forceinline__ void coll_cost_dist(const CollWarp& w, int S, const D
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULL_MASK, local, off);
   if (out.cost && lane == 0) *out.cost = local;
-  if (out.dist) {
+  if (F32 && out.dist) {
+    for (int wd = lane; wd < out.dist_words; wd += 32) out.dist[wd] = wd < S ? __float_as_uint(w.acc[wd].x) : 0u;
+  } else if (out.dist) {
     dispatch_kind(fD.kind, [&](auto kc) {
       constexpr int K = decltype(kc)::value;
       for (int wd = lane; wd < out.dist_words; wd += 32)
@@ -692,11 +706,12 @@ __device__ __forceinline__ void coll_reset(const CollWarp& w, int S, int lane) {
 }
 
 // Cost, the packed D (acc.x) and G (acc.yzw) rows of one configuration, one
-// word per lane; then zeroes acc.
+// word per lane; then zeroes acc.  F32: D and G are float32.
+template <bool F32 = false>
 __device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const DevFmt& fD, const DevFmt& fG,
                                              float w_c, float extra, const CollOut& out, int lane) {
-  coll_cost_dist(w, S, fD, w_c, extra, out, lane);
-  if (out.grad && fG.kind == KIND_F32) {  // float32: lane s writes sphere s's three words
+  coll_cost_dist<F32>(w, S, fD, w_c, extra, out, lane);
+  if (out.grad && (F32 || fG.kind == KIND_F32)) {  // float32: lane s writes sphere s's three words
     for (int s = lane; s < S; s += 32) {
       const float4 a = w.acc[s];
       uint32_t* r = out.grad + 3 * s;
@@ -705,7 +720,7 @@ __device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const Dev
       r[2] = __float_as_uint(a.w);
     }
     for (int wd = 3 * S + lane; wd < out.grad_words; wd += 32) out.grad[wd] = 0u;  // row padding
-  } else if (out.grad) {
+  } else if (!F32 && out.grad) {
     const int nv = 3 * S;
     dispatch_kind(fG.kind, [&](auto kc) {
       constexpr int K = decltype(kc)::value;
@@ -765,13 +780,15 @@ __device__ __forceinline__ void env_bits_direct(const SceneSm& m, int obase, uns
 // cluster pairs at a time are expanded into their pairs through a warp
 // prefix sum of their pair counts (lane t of a round finds its cluster pair
 // by binary search), and the pairs are tested in table order; each active
-// pair's gradient is added to its two spheres in that order, one pair at a
-// time.
+// pair's gradient is added to its two spheres in fixed point (w.gi), and
+// the sums are added to G at the end.
 __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m, const CollWarp& w,
                                             int S, float w_s, int lane) {
-  const int NC = rb.n_cl[0], NG = m.self_meta[0];
+  const int NC = rb.n_cl[0], NG = m.self_meta[0], e = rb.n_cl[1];
   const float eta_s = __int_as_float(m.self_meta[1]);
-  static_assert(CL == 3, "a cluster's spheres are packed three to a word");
+  const float fix = __int_as_float((127 + e) << 23);  // 2^e
+  for (int s = lane; s < S; s += 32) w.gi[s] = make_int4(0, 0, 0, 0);
+  static_assert(CL <= 3, "a cluster's spheres are packed, 8 bits each, in one word with their count");
   for (int c = lane; c < NC; c += 32) {
     const int packed = rb.cl_sph[c], cnt = packed >> 24;
     float4 p[CL];
@@ -838,63 +855,60 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
           if (__shfl_sync(FULL_MASK, incl, owner + step - 1) <= v) owner += step;
         const int pst = __shfl_sync(FULL_MASK, st, owner), pex = __shfl_sync(FULL_MASK, excl, owner);
         bool act = false;
-        float pen = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+        float pen = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;  // (c_i - c_j) / |c_i - c_j|
         int i = 0, j = 0;
         if (v < total) {
-          const uint2 pr = m.pairs[pst + v - pex];
-          i = (int)(pr.x & 0xffffu);
-          j = (int)(pr.x >> 16);
+          const uint32_t pr = m.pairs[pst + v - pex];
+          i = (int)(pr & 0xffffu);
+          j = (int)(pr >> 16);
           const float4 ci = w.P[i], cj = w.P[j];
           const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
           const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float thr = __uint_as_float(pr.y);
+          const float thr = (ci.w + cj.w) + eta_s;
           if (d2 < thr * thr) {
             const float rs = d2 > 0.f ? rsqrtf(d2) : 0.f;
             pen = thr - d2 * rs;
             act = pen > 0.f;
-            const float inv = w_s * rs;  // 0 at zero distance: no gradient
-            ux = dx * inv;
-            uy = dy * inv;
-            uz = dz * inv;
+            ux = dx * rs;  // 0 at zero distance: no gradient
+            uy = dy * rs;
+            uz = dz * rs;
           }
         }
-        // active pairs in table order (lane order within the round), one at
-        // a time, so every sphere receives its self terms in that order: the
-        // active lanes stage their pairs in lane order and lane 0 applies
-        // them (one divergent region and two warp barriers per round, not
-        // per pair).  (Measured and slower: each pair's own lane applying
-        // it, behind a warp barrier per pair; the owners of the spheres
-        // accumulating in registers from shuffled pairs; updating all at
-        // once when no two active pairs of a round share a sphere.)
-        const unsigned am = __ballot_sync(FULL_MASK, act);
+        // each active pair adds -u to sphere i and +u to sphere j, in fixed
+        // point (u times 2^e, rounded to an integer): integer sums do not
+        // depend on the order of the additions, so the lanes add them at
+        // once with shared-memory atomics and the result is still the same
+        // bits every time.  (Measured and slower: float sums in table order
+        // by lane 0 from staged pairs, which also set the launch's tail on
+        // configurations with many contacts; each pair's own lane applying
+        // it behind a warp barrier per pair; the spheres' owners receiving
+        // the pairs by shuffles or from shared memory.)
         if (act) {
           selfsum += pen;
-          w.stage[__popc(am & ((1u << lane) - 1u))] = make_float4(__int_as_float(i | (j << 16)), ux, uy, uz);
+          const int vx = __float2int_rn(ux * fix), vy = __float2int_rn(uy * fix), vz = __float2int_rn(uz * fix);
+          atomicAdd(&w.gi[i].x, -vx);
+          atomicAdd(&w.gi[i].y, -vy);
+          atomicAdd(&w.gi[i].z, -vz);
+          atomicAdd(&w.gi[j].x, vx);
+          atomicAdd(&w.gi[j].y, vy);
+          atomicAdd(&w.gi[j].z, vz);
         }
-        __syncwarp();
-        if (lane == 0) {
-          const int na = __popc(am);
-          for (int k = 0; k < na; ++k) {
-            const float4 e = w.stage[k];
-            const int pi = __float_as_int(e.x) & 0xffff, pj = __float_as_int(e.x) >> 16;
-            float4 ai = w.acc[pi], aj = w.acc[pj];  // both loads first (a pair with i == j has u = 0)
-            ai.y -= e.y;
-            ai.z -= e.z;
-            ai.w -= e.w;
-            aj.y += e.y;
-            aj.z += e.z;
-            aj.w += e.w;
-            w.acc[pi] = ai;
-            w.acc[pj] = aj;
-          }
-        }
-        __syncwarp();
       }
     }
     __syncwarp();  // w.kept is rewritten by the next KEPT_CAP
   }
   __syncwarp();
-  (void)S;
+  // G += w_s 2^-e (the fixed-point sums)
+  const float unit = w_s * __int_as_float((127 - e) << 23);
+  for (int s = lane; s < S; s += 32) {
+    float4 a = w.acc[s];
+    const int4 g = w.gi[s];
+    a.y = fmaf(unit, (float)g.x, a.y);
+    a.z = fmaf(unit, (float)g.y, a.z);
+    a.w = fmaf(unit, (float)g.z, a.w);
+    w.acc[s] = a;
+  }
+  __syncwarp();
   return selfsum;
 }
 
@@ -1001,7 +1015,7 @@ __device__ __forceinline__ float collision_terms(const RobotArgs& r, int O, cons
 // COHERENT reads the P row with loads that see writes made earlier in the
 // same kernel (the fused multi-problem kernel); otherwise through the
 // read-only cache.
-template <bool COHERENT = false, bool MASKED = false, typename Between = NoHook>
+template <bool COHERENT = false, bool MASKED = false, bool F32 = false, typename Between = NoHook>
 __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, const RobotSm& rb,
                                                  const SceneSm& m, const CollWarp& w,
                                                  const uint32_t* prow, const DevFmt& fP,
@@ -1012,13 +1026,13 @@ __device__ __forceinline__ void collision_config(const RobotArgs& r, int O, cons
                                                  const GridHeader* grid = nullptr,
                                                  const uint2* cells = nullptr, Between between = Between{}) {
   // ---- 1. sphere centres (one word per lane)
-  load_centres<COHERENT>(prow, fP, r.S, w.P, lane);
+  load_centres<COHERENT, F32>(prow, fP, r.S, w.P, lane);
   __syncwarp();
   // ---- 2.-4. environment and self terms
   const float selfsum =
       collision_terms<MASKED>(r, O, rb, m, w, eta, w_c, w_s, lane, est, margin, grid, cells, between);
   // ---- 5. cost and packed outputs, then reset acc
-  coll_outputs(w, r.S, fD, fG, w_c, w_s * selfsum, out, lane);
+  coll_outputs<F32>(w, r.S, fD, fG, w_c, w_s * selfsum, out, lane);
 }
 
 // ------------------------------------------------------- backward (thread)

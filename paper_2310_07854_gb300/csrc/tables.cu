@@ -3,8 +3,7 @@
 // pair (the broad phase of iteration step 3 of Sec. III-B), built once by
 // the same block-cooperative code the kernels run (load_robot,
 // load_clusters, load_self) and stored in global memory for blocks to copy
-// (load_robot_self in stages.cuh).  The pair thresholds are stored without
-// eta_s, which the copy adds.
+// (load_robot_self in stages.cuh).
 #include "stages.cuh"
 
 namespace vapr {
@@ -20,7 +19,7 @@ struct TablesSm {
 __host__ __device__ inline void carve_tables(Bump& b, const RobotArgs& r, TablesSm& s) {
   carve_robot(b, r.J, r.S, s.rb);
   carve_scene(b, 0, r.NP, cluster_bound(r.S, r.J), s.sm);
-  carve_self_scratch(b, r.NP, cluster_bound(r.S, r.J), s.t);
+  carve_self_scratch(b, r.NP, cluster_bound(r.S, r.J), r.S, s.t);
 }
 
 __device__ __forceinline__ void store_granules(void* dst, const void* src, size_t bytes) {
@@ -37,7 +36,7 @@ __global__ void __launch_bounds__(TB_THREADS) robot_tables_kernel(RobotArgs r, u
   load_robot(r, s.rb);
   __syncthreads();
   load_clusters(r.J, r.S, s.rb);
-  load_self(r, s.rb, s.sm, s.t, 0.f);  // thresholds r_i + r_j
+  load_self(r, s.rb, s.sm, s.t, 0.f);  // (eta_s is not part of the tables)
   __shared__ uint32_t s_hash;
   if (threadIdx.x == 0) s_hash = 0u;
   __syncthreads();
@@ -54,8 +53,8 @@ __global__ void __launch_bounds__(TB_THREADS) robot_tables_kernel(RobotArgs r, u
   store_granules(im.rb.cl_start, s.rb.cl_start, (NCB + 1) * sizeof(int));
   store_granules(im.rb.cl_of, s.rb.cl_of, S * sizeof(int));
   store_granules(im.rb.cl_sph, s.rb.cl_sph, NCB * sizeof(int));
-  store_granules(im.rb.n_cl, s.rb.n_cl, sizeof(int));
-  store_granules(im.pairs, s.sm.pairs, r.NP * sizeof(uint2));
+  store_granules(im.rb.n_cl, s.rb.n_cl, 2 * sizeof(int));
+  store_granules(im.pairs, s.sm.pairs, r.NP * sizeof(uint32_t));
   store_granules(im.cp, s.sm.cp, NG * sizeof(uint16_t));
   store_granules(im.cp_start, s.sm.cp_start, (NG + 1) * sizeof(uint16_t));
   __syncthreads();
