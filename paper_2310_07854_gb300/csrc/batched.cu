@@ -82,11 +82,7 @@ __host__ __device__ inline void carve_batch(Bump& b, const BatchArgs& a, RobotSm
   carve_scene(b, a.maxO, a.maxNP, cluster_bound(a.maxS, a.maxJ), sm);
   Bump t(b.base);
   t.off = b.bytes();
-  for (int w = 0; w < BT_WARPS; ++w) {
-    CollWarp cw;
-    carve_coll_warp(b, a.maxS, a.maxJ, cw);
-    if (w == mine) w_mine = cw;
-  }
+  carve_warps(b, BT_WARPS, mine, [&](Bump& wb) { carve_coll_warp(wb, a.maxS, a.maxJ, w_mine); });
   const int tstride = (3 * a.maxJ) | 1, kstride = (2 * a.maxJ) | 1;
   sU = b.take<float4>((size_t)a.tile * (tstride > kstride ? tstride : kstride));  // T, then K
   sQ = b.take<float>((size_t)a.tile * a.maxJ);

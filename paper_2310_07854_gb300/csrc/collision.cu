@@ -80,11 +80,7 @@ __host__ __device__ inline void carve_coll(Bump& b, const RobotArgs& r, int O, R
   carve_scene(b, O, r.NP, cluster_bound(r.S, r.J), sm);
   Bump t(b.base);
   t.off = b.bytes();
-  for (int w = 0; w < COLL_WARPS; ++w) {
-    CollWarp cw;
-    carve_coll_warp(b, r.S, r.J, cw);
-    if (w == mine) w_mine = cw;
-  }
+  carve_warps(b, COLL_WARPS, mine, [&](Bump& wb) { carve_coll_warp(wb, r.S, r.J, w_mine); });
   carve_self_scratch(t, r.NP, cluster_bound(r.S, r.J), r.S, scratch);
   if (t.off > b.off) b.off = t.off;
 }

@@ -68,23 +68,15 @@ __host__ __device__ inline void carve_fused(Bump& b, const FusedArgs& a, RobotSm
   carve_scene(b, a.sc.O, r.NP, cluster_bound(r.S, r.J), sm);
   Bump t(b.base);
   t.off = b.bytes();
-  for (int w = 0; w < FU_WARPS; ++w) {
-    CollWarp cw;
-    carve_coll_warp(b, r.S, r.J, cw);
-    FusedWarp fw;
-    fw.lk = b.take<float4>(2 * VAPR_MAX_JOINTS);
-    fw.jrow = b.take<float>(VAPR_MAX_JOINTS);
-    if (w == mine) {
-      w_mine = cw;
-      f_mine = fw;
-    }
-  }
+  carve_warps(b, FU_WARPS, mine, [&](Bump& wb) {
+    carve_coll_warp(wb, r.S, r.J, w_mine);
+    f_mine.lk = wb.take<float4>(2 * VAPR_MAX_JOINTS);
+    f_mine.jrow = wb.take<float>(VAPR_MAX_JOINTS);
+  });
   carve_self_scratch(t, r.NP, cluster_bound(r.S, r.J), r.S, scratch);  // over the warps' sets (built first)
   if (t.off > b.off) b.off = t.off;
-  for (int w = 0; w < FU_WARPS; ++w) {  // (after the scratch: written once the tables are built)
-    float4* T = b.take<float4>((size_t)FU_MT * a.tstride);
-    if (w == mine) f_mine.T = T;
-  }
+  // (after the scratch: written once the tables are built)
+  carve_warps(b, FU_WARPS, mine, [&](Bump& wb) { f_mine.T = wb.take<float4>((size_t)FU_MT * a.tstride); });
 }
 
 // dec(enc(x)) in format f: the value a stored and reloaded x has.
@@ -92,6 +84,9 @@ __device__ __forceinline__ float round_trip(float x, const DevFmt& f) {
   return f.kind == KIND_F32 ? x : decode(encode(x, f), f);
 }
 
+// F32: P, G, D and J are float32 (the loop body without the other formats'
+// code, for the instruction cache).
+template <bool F32>
 __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -137,7 +132,8 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
         const float cy = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
         const float cz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
         const float4 old = w.P[s];  // .w: the radius
-        w.P[s] = make_float4(round_trip(cx, a.fP), round_trip(cy, a.fP), round_trip(cz, a.fP), old.w);
+        w.P[s] = F32 ? make_float4(cx, cy, cz, old.w)
+                     : make_float4(round_trip(cx, a.fP), round_trip(cy, a.fP), round_trip(cz, a.fP), old.w);
       }
       __syncwarp();
       // ---- collision: environment and self terms, cost and D out
@@ -149,12 +145,12 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
       out.dist_words = (int)(a.dist.stride / 4);
       out.grad = nullptr;
       out.grad_words = 0;
-      coll_cost_dist(w, S, a.dist.f, a.w_c, a.w_s * selfsum, out, lane);
+      coll_cost_dist<F32>(w, S, a.dist.f, a.w_c, a.w_s * selfsum, out, lane);
       __syncwarp();
       // ---- backward: G rounded to its format (lanes over spheres), then
       //      lane l forms link l's sums and moment, and lane j runs the
       //      staged pass's running totals over the links to form J_j
-      if (a.fG.kind != KIND_F32) {
+      if (!F32 && a.fG.kind != KIND_F32) {
         for (int s = lane; s < S; s += 32) {
           const float4 gg = w.acc[s];
           w.acc[s] = make_float4(gg.x, round_trip(gg.y, a.fG), round_trip(gg.z, a.fG), round_trip(gg.w, a.fG));
@@ -205,10 +201,16 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
       __syncwarp();
       {
         uint4* row = reinterpret_cast<uint4*>(a.jgrad.ptr + c * a.jgrad.stride);
-        for (int cc = lane; cc < (int)(a.jgrad.stride / 16); cc += 32)
-          row[cc] = pack_chunk_dyn(cc, J, a.jgrad.f, [&](int i2) { return fw.jrow[i2]; });
+        for (int cc = lane; cc < (int)(a.jgrad.stride / 16); cc += 32) {
+          if constexpr (F32) {
+            auto v = [&](int i2) { return i2 < J ? __float_as_uint(fw.jrow[i2]) : 0u; };
+            row[cc] = make_uint4(v(4 * cc), v(4 * cc + 1), v(4 * cc + 2), v(4 * cc + 3));
+          } else {
+            row[cc] = pack_chunk_dyn(cc, J, a.jgrad.f, [&](int i2) { return fw.jrow[i2]; });
+          }
+        }
       }
-      coll_reset(w, S, lane);
+      __syncwarp();  // (collision_terms rewrites acc whole for the next configuration)
     }
   }
 }
@@ -240,14 +242,17 @@ cudaError_t launch_fused(const RobotArgs& r, const SceneArgs& sc, const vapr_cos
   SelfScratch scratch;
   carve_fused(b, a, rb, sm, w, fw, 0, scratch);
   const size_t smem = b.bytes();
-  const int per_sm = blocks_per_sm((const void*)fused_kernel, FU_WARPS * 32, smem);
+  const bool f32 = a.fP.kind == KIND_F32 && a.fG.kind == KIND_F32 && jgrad.f.kind == KIND_F32 &&
+                   (!dist.ptr || dist.f.kind == KIND_F32);
+  auto kernel = f32 ? fused_kernel<true> : fused_kernel<false>;
+  const int per_sm = blocks_per_sm((const void*)kernel, FU_WARPS * 32, smem);
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   const int64_t n_mt = (n + FU_MT - 1) / FU_MT;
   const int64_t cap = (int64_t)sm_count() * per_sm;
   const int64_t want = (n_mt + FU_WARPS - 1) / FU_WARPS;  // at least a mini-tile per warp
   const int grid = (int)(want < cap ? want : cap);
   a.mt_per_block = (n_mt + grid - 1) / grid;
-  fused_kernel<<<grid, FU_WARPS * 32, smem, st>>>(a);
+  kernel<<<grid, FU_WARPS * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,22 @@ struct Bump {
   __host__ __device__ size_t bytes() const { return (off + 15) & ~(size_t)15; }
 };
 
+// nw equal per-warp working sets, carve(Bump&) each, one after another from
+// b's next 16-byte boundary: the layout of nw calls of carve(b) in turn,
+// computed with two calls (one for the stride, one for warp mine's
+// pointers, left in carve's outputs).
+template <typename Carve>
+__host__ __device__ inline void carve_warps(Bump& b, int nw, int mine, Carve carve) {
+  Bump probe(nullptr);
+  carve(probe);
+  const size_t stride = probe.bytes();
+  b.off = b.bytes();
+  Bump mb(b.base);
+  mb.off = b.off + (size_t)mine * stride;
+  carve(mb);
+  b.off += (size_t)nw * stride;
+}
+
 // ------------------------------------------------------------ robot tables
 // Self-collision clusters: runs of at most CL consecutive spheres of one
 // link (in the link-grouped order), at most cluster_bound(S, J) of them.
@@ -506,11 +522,11 @@ __device__ inline void load_robot_self(const RobotArgs& r, const RobotSm& rb, co
   __shared__ int s_ok;
   const TablesHeader* h = static_cast<const TablesHeader*>(r.tables);
   bool ok = false;
+  Bump b(const_cast<void*>(r.tables));
+  RobotImage im;
   if (h) {  // uniform over the block
-    Bump b0(nullptr);
-    RobotImage im0;
-    carve_image(b0, r.J, r.S, r.NP, im0);
-    const uint32_t nw = (uint32_t)((b0.bytes() - sizeof(TablesHeader)) / 4);
+    carve_image(b, r.J, r.S, r.NP, im);
+    const uint32_t nw = (uint32_t)((b.bytes() - sizeof(TablesHeader)) / 4);
     if (threadIdx.x == 0) {
       s_hash = 0u;
       s_body = 0u;
@@ -534,22 +550,36 @@ __device__ inline void load_robot_self(const RobotArgs& r, const RobotSm& rb, co
     load_self(r, rb, m, t, eta_s);
     return;
   }
-  Bump b(const_cast<void*>(r.tables));
-  RobotImage im;
-  carve_image(b, r.J, r.S, r.NP, im);
   const int J = r.J, S = r.S, NCB = cluster_bound(S, J), NG = (int)h->NG;
-  copy_granules(rb.F, im.rb.F, 3 * J * sizeof(float4));
-  copy_granules(rb.sph, im.rb.sph, S * sizeof(float4));
-  copy_granules(rb.link0, im.rb.link0, S * sizeof(int));
-  copy_granules(rb.order, im.rb.order, S * sizeof(int));
-  copy_granules(rb.start, im.rb.start, (J + 1) * sizeof(int));
-  copy_granules(rb.cl_start, im.rb.cl_start, (NCB + 1) * sizeof(int));
-  copy_granules(rb.cl_of, im.rb.cl_of, S * sizeof(int));
-  copy_granules(rb.cl_sph, im.rb.cl_sph, NCB * sizeof(int));
-  copy_granules(rb.n_cl, im.rb.n_cl, 2 * sizeof(int));
-  copy_granules(m.cp, im.cp, NG * sizeof(uint16_t));
-  copy_granules(m.cp_start, im.cp_start, (NG + 1) * sizeof(uint16_t));
-  copy_granules(m.pairs, im.pairs, r.NP * sizeof(uint32_t));
+  const char *ib = reinterpret_cast<const char*>(im.rb.F), *sb = reinterpret_cast<const char*>(rb.F);
+  const char *ip = reinterpret_cast<const char*>(im.pairs), *sp = reinterpret_cast<const char*>(m.pairs);
+  // the robot arrays, and the pair tables, lie in the same order and
+  // alignment in the image as in a block carved for this robot's sizes:
+  // one copy each then
+  const bool same_robot = reinterpret_cast<const char*>(rb.n_cl) - sb == reinterpret_cast<const char*>(im.rb.n_cl) - ib &&
+                          reinterpret_cast<const char*>(rb.cl_of) - sb == reinterpret_cast<const char*>(im.rb.cl_of) - ib;
+  const bool same_self = reinterpret_cast<const char*>(m.cp) - sp == reinterpret_cast<const char*>(im.cp) - ip &&
+                         reinterpret_cast<const char*>(m.cp_start) - sp == reinterpret_cast<const char*>(im.cp_start) - ip;
+  if (same_robot) {
+    copy_granules(rb.F, im.rb.F, reinterpret_cast<const char*>(im.rb.n_cl + 2) - ib);
+  } else {
+    copy_granules(rb.F, im.rb.F, 3 * J * sizeof(float4));
+    copy_granules(rb.sph, im.rb.sph, S * sizeof(float4));
+    copy_granules(rb.link0, im.rb.link0, S * sizeof(int));
+    copy_granules(rb.order, im.rb.order, S * sizeof(int));
+    copy_granules(rb.start, im.rb.start, (J + 1) * sizeof(int));
+    copy_granules(rb.cl_start, im.rb.cl_start, (NCB + 1) * sizeof(int));
+    copy_granules(rb.cl_of, im.rb.cl_of, S * sizeof(int));
+    copy_granules(rb.cl_sph, im.rb.cl_sph, NCB * sizeof(int));
+    copy_granules(rb.n_cl, im.rb.n_cl, 2 * sizeof(int));
+  }
+  if (same_self) {
+    copy_granules(m.pairs, im.pairs, reinterpret_cast<const char*>(im.cp_start + NG + 1) - ip);
+  } else {
+    copy_granules(m.cp, im.cp, NG * sizeof(uint16_t));
+    copy_granules(m.cp_start, im.cp_start, (NG + 1) * sizeof(uint16_t));
+    copy_granules(m.pairs, im.pairs, r.NP * sizeof(uint32_t));
+  }
   if (threadIdx.x == 0) {
     m.self_meta[0] = NG;
     m.self_meta[1] = (int)__float_as_uint(eta_s);
@@ -706,7 +736,8 @@ __device__ __forceinline__ void coll_reset(const CollWarp& w, int S, int lane) {
 }
 
 // Cost, the packed D (acc.x) and G (acc.yzw) rows of one configuration, one
-// word per lane; then zeroes acc.  F32: D and G are float32.
+// word per lane (every caller rewrites acc whole for the next configuration,
+// after the closing warp barrier).  F32: D and G are float32.
 template <bool F32 = false>
 __device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const DevFmt& fD, const DevFmt& fG,
                                              float w_c, float extra, const CollOut& out, int lane) {
@@ -731,7 +762,7 @@ __device__ __forceinline__ void coll_outputs(const CollWarp& w, int S, const Dev
         });
     });
   }
-  coll_reset(w, S, lane);
+  __syncwarp();
 }
 
 // Environment terms of sphere p over the cuboids obase + b for the set bits

@@ -39,17 +39,11 @@ __host__ __device__ inline void carve_swept(Bump& b, const RobotArgs& r, int O, 
                                             CollWarp& w_mine, float4*& Pn, float4*& Pp, int mine) {
   carve_robot(b, r.J, r.S, rb);
   carve_scene(b, O, 0, 0, sm);
-  for (int w = 0; w < SW_WARPS; ++w) {
-    CollWarp t;
-    carve_coll_warp(b, r.S, r.J, t);
-    float4* n = b.take<float4>(r.S);
-    float4* p = b.take<float4>(r.S);
-    if (w == mine) {
-      w_mine = t;
-      Pn = n;
-      Pp = p;
-    }
-  }
+  carve_warps(b, SW_WARPS, mine, [&](Bump& wb) {
+    carve_coll_warp(wb, r.S, r.J, w_mine);
+    Pn = wb.take<float4>(r.S);
+    Pp = wb.take<float4>(r.S);
+  });
 }
 
 // Hinge terms of the point (x, radius x.w) against every cuboid, into t.
