@@ -818,6 +818,7 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
   const int NC = rb.n_cl[0], NG = m.self_meta[0], e = rb.n_cl[1];
   const float eta_s = __int_as_float(m.self_meta[1]);
   const float fix = __int_as_float((127 + e) << 23);  // 2^e
+  const float eta_m = eta_s + 1e-4f;                  // eta_s and the margin's 1e-4 m
   for (int s = lane; s < S; s += 32) w.gi[s] = make_int4(0, 0, 0, 0);
   static_assert(CL <= 3, "a cluster's spheres are packed, 8 bits each, in one word with their count");
   for (int c = lane; c < NC; c += 32) {
@@ -844,7 +845,9 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
         // |c_s - centroid| from the hardware reciprocal square root, rounded up
         rho = fmaxf(rho, fmaf(e2 > 0.f ? e2 * rsqrtf(e2) : 0.f, 1.000001f, p[k].w));
       }
-    w.cls[c] = make_float4(cx, cy, cz, rho);
+    // grown by this cluster's share of the test's rounding margin,
+    // 4e-6 (|centre|_1 + rho) (the pair test adds 1e-4 m on top)
+    w.cls[c] = make_float4(cx, cy, cz, fmaf(4e-6f, fabsf(cx) + fabsf(cy) + fabsf(cz) + rho, rho));
   }
   __syncwarp();
   float selfsum = 0.f;
@@ -860,8 +863,7 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
         const float4 A = w.cls[ab & 0xffu], B = w.cls[ab >> 8];
         const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float mag = fabsf(A.x) + fabsf(A.y) + fabsf(A.z) + fabsf(B.x) + fabsf(B.y) + fabsf(B.z);
-        const float rhs = A.w + B.w + eta_s + fmaf(4e-6f, mag + A.w + B.w, 1e-4f);
+        const float rhs = A.w + B.w + eta_m;
         keep = !(rhs <= 0.f || d2 >= rhs * rhs);
       }
       const unsigned km = __ballot_sync(FULL_MASK, keep);
@@ -878,13 +880,17 @@ __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m,
       }
       const int incl = warp_scan(cnt, lane), excl = incl - cnt;
       const int total = __shfl_sync(FULL_MASK, incl, 31);
+      int before = 0;  // listed cluster pairs whose pairs start before t0
       for (int t0 = 0; t0 < total; t0 += 32) {
         const int v = t0 + lane;
-        int owner = 0;  // first lane whose inclusive count exceeds v
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (__shfl_sync(FULL_MASK, incl, owner + step - 1) <= v) owner += step;
-        const int pst = __shfl_sync(FULL_MASK, st, owner), pex = __shfl_sync(FULL_MASK, excl, owner);
+        // the cluster pairs whose pairs start in [t0, t0 + 32), as bits
+        // (every listed cluster pair has at least one pair): v's owner is
+        // the last of them starting at or before v
+        const unsigned starts =
+            __reduce_or_sync(FULL_MASK, cnt > 0 && excl >= t0 && excl < t0 + 32 ? 1u << (excl - t0) : 0u);
+        const int owner = before + __popc(starts & ((2u << lane) - 1u)) - 1;
+        before += __popc(starts);
+        const int pst = __shfl_sync(FULL_MASK, st, owner & 31), pex = __shfl_sync(FULL_MASK, excl, owner & 31);
         bool act = false;
         float pen = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;  // (c_i - c_j) / |c_i - c_j|
         int i = 0, j = 0;
