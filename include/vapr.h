@@ -237,8 +237,11 @@ vapr_status vapr_fk(const vapr_robot* robot, const float* q, int64_t n,
  * table->grad.  The environment sum runs over every cuboid; the hinge's
  * gradient at exactly zero penetration is 0, and a self pair at zero
  * distance adds no gradient.  Each configuration's outputs depend on that
- * configuration alone (fixed summation orders), whatever the batch, the
- * scene grid or the order in which the kernel's warps take configurations.
+ * configuration alone (fixed summation orders; the self pairs' gradient
+ * terms are summed as integers, u times 2^e rounded, e set by the most
+ * pairs naming one sphere, so their order does not matter), whatever the
+ * batch, the scene grid or the order in which the kernel's warps take
+ * configurations.
  * Launches made outside stream capture may overlap one another (on other
  * streams or host threads), and so may successive replays of one
  * instantiated graph, which CUDA runs one after another.  A launch captured
