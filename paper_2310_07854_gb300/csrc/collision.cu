@@ -97,11 +97,10 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
   CollWarp w;
   SelfScratch scratch;
   carve_coll(b, a.r, a.sc.O, rb, sm, w, wid, scratch);
-  load_scene(a.r, a.sc, a.eta, a.eta_s, sm);
-  load_robot_self(a.r, rb, sm, scratch, a.eta_s);
-  init_coll_warp(a.r, w, lane);
-  __syncthreads();
-  const GridHeader* grid = grid_check(a.sc, a.r, a.eta);  // null: visit every cuboid
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_next = 0;  // (visible after the prologue's barriers)
+  // null grid: visit every cuboid
+  const GridHeader* grid = load_block_tables(a.r, a.sc, a.eta, a.eta_s, rb, sm, scratch, w);
   const uint2* cells = grid ? grid_cells(a.sc) : nullptr;
 
   CollOut out;
@@ -109,12 +108,9 @@ __global__ void __launch_bounds__(COLL_WARPS * 32, 4) collision_kernel(CollArgs 
   out.grad_words = (int)(a.grad.stride / 4);
   // configurations come one at a time per warp: from the launch's ticket
   // slot, or (no slot) from a shared counter over the block's contiguous range
-  __shared__ int s_next;
   const int64_t per_block = (a.n + gridDim.x - 1) / gridDim.x;
   const int64_t c_begin = a.slot >= 0 ? 0 : blockIdx.x * per_block;
   const int64_t c_end = a.slot >= 0 ? a.n : (c_begin + per_block < a.n ? c_begin + per_block : a.n);
-  if (threadIdx.x == 0) s_next = 0;
-  __syncthreads();
   grid_dependents_may_launch();  // (the next stage waits for this grid to finish)
   grid_dependency_wait();        // the P rows are complete from here on
   auto draw = [&]() -> unsigned int {  // lane 0's ticket (the other lanes get 0)

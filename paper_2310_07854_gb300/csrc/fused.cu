@@ -98,13 +98,10 @@ __global__ void __launch_bounds__(FU_WARPS * 32, 4) fused_kernel(FusedArgs a) {
   FusedWarp fw;
   SelfScratch scratch;
   carve_fused(b, a, rb, sm, w, fw, wid, scratch);
-  load_scene(a.r, a.sc, a.eta, a.eta_s, sm);
-  load_robot_self(a.r, rb, sm, scratch, a.eta_s);
-  init_coll_warp(a.r, w, lane);
   __shared__ int s_next;
-  if (threadIdx.x == 0) s_next = 0;
-  __syncthreads();
-  const GridHeader* grid = grid_check(a.sc, a.r, a.eta);  // null: visit every cuboid
+  if (threadIdx.x == 0) s_next = 0;  // (visible after the prologue's barriers)
+  // null grid: visit every cuboid
+  const GridHeader* grid = load_block_tables(a.r, a.sc, a.eta, a.eta_s, rb, sm, scratch, w);
   const uint2* cells = grid ? grid_cells(a.sc) : nullptr;
 
   const int64_t n_mt = (a.n + FU_MT - 1) / FU_MT;

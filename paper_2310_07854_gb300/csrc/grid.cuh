@@ -89,6 +89,18 @@ __device__ __forceinline__ float grid_reach_of(const SceneArgs& sc, int o, float
   return fabsf(sqrtf(hx * hx + hy * hy + hz * hz) + eta + SLACK) + reach;
 }
 
+// Whether header g was built for this scene (hash: the scene's current
+// hash), this eta and radii covering every sphere (rmin, rmax: the
+// smallest and largest radius as int bits; non-negative floats order like
+// their bits, and a negative radius, -0 or a NaN fails the range check).
+__device__ __forceinline__ bool grid_header_ok(const GridHeader& g, const SceneArgs& sc, float eta, uint32_t hash,
+                                               int rmin, int rmax) {
+  return g.magic == GRID_MAGIC && g.O == sc.O && g.eta_bits == __float_as_uint(eta) && g.hash == hash &&
+         rmin >= 0 && rmax <= __float_as_int(g.reach) && g.words == grid_words(sc.O) && g.dims[0] >= 0 &&
+         g.dims[0] <= GRID_MAX_CELLS && g.dims[1] >= 0 && g.dims[1] <= GRID_MAX_CELLS && g.dims[2] >= 0 &&
+         g.dims[2] <= GRID_MAX_CELLS;
+}
+
 // Block-cooperative (every thread calls it; the block must be converged):
 // a shared-memory copy of the scene's grid header when the grid was built
 // for this scene's current contents, this eta and radii covering every
@@ -118,15 +130,7 @@ __device__ inline const GridHeader* grid_check(const SceneArgs& sc, const RobotA
   if (threadIdx.x < (int)(sizeof(GridHeader) / 4))
     reinterpret_cast<uint32_t*>(&s_g)[threadIdx.x] = reinterpret_cast<const uint32_t*>(g)[threadIdx.x];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // radii as int bits: non-negative floats order like their bits, and a
-    // negative radius, -0 or a NaN fails the range check
-    s_ok = s_g.magic == GRID_MAGIC && s_g.O == sc.O && s_g.eta_bits == __float_as_uint(eta) &&
-           s_g.hash == s_hash && s_rmin >= 0 && s_rmax <= __float_as_int(s_g.reach) &&
-           s_g.words == grid_words(sc.O) && s_g.dims[0] >= 0 && s_g.dims[0] <= GRID_MAX_CELLS &&
-           s_g.dims[1] >= 0 && s_g.dims[1] <= GRID_MAX_CELLS && s_g.dims[2] >= 0 &&
-           s_g.dims[2] <= GRID_MAX_CELLS;
-  }
+  if (threadIdx.x == 0) s_ok = grid_header_ok(s_g, sc, eta, s_hash, s_rmin, s_rmax);
   __syncthreads();
   return s_ok ? &s_g : nullptr;
 }

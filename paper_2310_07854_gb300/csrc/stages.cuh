@@ -614,6 +614,107 @@ __device__ __forceinline__ void init_coll_warp(const RobotArgs& r, const CollWar
   }
 }
 
+// Block-cooperative prologue of a block carved for this robot's own sizes
+// (every thread calls it, the block converged): the scene arrays
+// (load_scene), the robot and self tables (as load_robot_self: copied from
+// r.tables when they were made for this robot, else built) and the scene
+// grid's header (as grid_check: null when there is no usable grid), with
+// every global read of the checks and the copies issued in one phase: the
+// three hashes are summed per warp and checked by thread 0 behind one
+// barrier, and the tables are copied before their check (a failed check
+// builds them over the copy; the copy reads only as far as the image's own
+// header says it reaches).  Then each warp's working set (init_coll_warp,
+// radii from the tables).  Three block barriers; ends with the block
+// synchronised.
+__device__ inline const GridHeader* load_block_tables(const RobotArgs& r, const SceneArgs& sc, float eta,
+                                                      float eta_s, const RobotSm& rb, const SceneSm& m,
+                                                      const SelfScratch& t, const CollWarp& w) {
+  __shared__ uint32_t s_part[32][3];  // per warp: robot, body and scene hash shares
+  __shared__ int s_rad[32][2];        // per warp: smallest and largest radius bits
+  __shared__ GridHeader s_g;
+  __shared__ int s_ok[2];             // tables, grid
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (int)(blockDim.x >> 5);
+  const TablesHeader* h = static_cast<const TablesHeader*>(r.tables);
+  const GridHeader* g = static_cast<const GridHeader*>(sc.grid);
+  load_scene(r, sc, eta, eta_s, m);
+  uint32_t hr = 0u, hb = 0u, hs = 0u;
+  int rmin = 0x7fffffff, rmax = (int)0x80000000;
+  bool sized = false;
+  if (h) {  // uniform over the block
+    Bump b(const_cast<void*>(r.tables));
+    RobotImage im;
+    carve_image(b, r.J, r.S, r.NP, im);
+    const uint32_t nw = (uint32_t)((b.bytes() - sizeof(TablesHeader)) / 4);
+    hr = robot_hash_part(r, threadIdx.x, blockDim.x);
+    sized = __ldcg(&h->body_words) == nw;  // the reads below stay inside the image
+    if (sized) {
+      hb = body_hash_part(reinterpret_cast<const uint32_t*>(h + 1), nw, threadIdx.x, blockDim.x);
+      const int NGb = pair_groups_bound(r.NP, cluster_bound(r.S, r.J));
+      copy_granules(rb.F, im.rb.F, reinterpret_cast<const char*>(im.rb.n_cl + 2) - reinterpret_cast<const char*>(im.rb.F));
+      copy_granules(m.pairs, im.pairs, reinterpret_cast<const char*>(im.cp_start + NGb + 1) -
+                                           reinterpret_cast<const char*>(im.pairs));
+    }
+  }
+  if (g) {
+    hs = scene_hash_part(sc, threadIdx.x, blockDim.x);
+    for (int s = threadIdx.x; s < r.S; s += blockDim.x) {
+      const int bits = __float_as_int(r.sphere_local[4 * s + 3]);
+      rmin = min(rmin, bits);
+      rmax = max(rmax, bits);
+    }
+    if (threadIdx.x < (int)(sizeof(GridHeader) / 4))
+      reinterpret_cast<uint32_t*>(&s_g)[threadIdx.x] = reinterpret_cast<const uint32_t*>(g)[threadIdx.x];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    hr += __shfl_xor_sync(FULL_MASK, hr, off);
+    hb += __shfl_xor_sync(FULL_MASK, hb, off);
+    hs += __shfl_xor_sync(FULL_MASK, hs, off);
+    rmin = min(rmin, __shfl_xor_sync(FULL_MASK, rmin, off));
+    rmax = max(rmax, __shfl_xor_sync(FULL_MASK, rmax, off));
+  }
+  if (lane == 0) {
+    s_part[warp][0] = hr;
+    s_part[warp][1] = hb;
+    s_part[warp][2] = hs;
+    s_rad[warp][0] = rmin;
+    s_rad[warp][1] = rmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t sr = 0u, sb = 0u, ss = 0u;
+    int mn = 0x7fffffff, mx = (int)0x80000000;
+    for (int k = 0; k < nwarps; ++k) {
+      sr += s_part[k][0];
+      sb += s_part[k][1];
+      ss += s_part[k][2];
+      mn = min(mn, s_rad[k][0]);
+      mx = max(mx, s_rad[k][1]);
+    }
+    const bool tok = h && sized && h->magic == TABLES_MAGIC && h->J == (uint32_t)r.J && h->S == (uint32_t)r.S &&
+                     h->NP == (uint32_t)r.NP && h->hash == sr && h->body_hash == sb;
+    s_ok[0] = tok;
+    s_ok[1] = g && grid_header_ok(s_g, sc, eta, ss, mn, mx);
+    if (tok) {
+      m.self_meta[0] = (int)h->NG;
+      m.self_meta[1] = (int)__float_as_uint(eta_s);
+    }
+  }
+  __syncthreads();
+  if (!s_ok[0]) {  // uniform: build the tables over whatever was copied
+    load_robot(r, rb);
+    __syncthreads();
+    load_clusters(r.J, r.S, rb);
+    load_self(r, rb, m, t, eta_s);
+  }
+  for (int s = lane; s < r.S; s += 32) {  // this warp's working set (over the scratch)
+    w.P[s] = make_float4(0.f, 0.f, 0.f, rb.sph[s].w);
+    w.acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  return s_ok[1] ? &s_g : nullptr;
+}
+
 // Exact sphere-cuboid term: penetration max(0, r + eta - d) of the sphere
 // (c, c.w = r) against cuboid o, and its gradient -w_c grad d, as
 // (D, gx, gy, gz); all zero when the sphere is clear of the cuboid.
