@@ -189,7 +189,8 @@ def _big_robot():
 
 
 @pytest.mark.parametrize("case", ["n1", "n129", "n1000_no_pairs", "one_sphere", "no_cuboids",
-                                  "max_sizes", "shuffled_spheres", "reversed_pairs", "duplicate_pairs"])
+                                  "max_sizes", "shuffled_spheres", "reversed_pairs", "duplicate_pairs",
+                                  "heavy_duplicates"])
 def test_edge_cases(case):
     robot, n, O = synth.make_robot(2), 64, 8
     if case == "n1":
@@ -219,6 +220,14 @@ def test_edge_cases(case):
         extra = np.concatenate([pr[:40], pr[100:101, ::-1]])
         robot = synth.Robot(robot.joint_fixed, robot.sphere_local, robot.sphere_link,
                             np.ascontiguousarray(np.concatenate([pr, extra]).astype(np.int32)))
+    elif case == "heavy_duplicates":  # one always-overlapping pair named 6000 times: the
+        # fixed-point self sums of its two spheres take a coarse exponent and must not
+        # overflow.  Its spheres are on links 1 and 2, so the pair turns joint 2 (a pair
+        # within one link would cancel in J, leaving float32 rounding of 6000-fold terms)
+        pr = np.asarray(robot.pairs)
+        extra = np.tile(np.array([[4, 5]], np.int32), (6000, 1))
+        robot = synth.Robot(robot.joint_fixed, robot.sphere_local, robot.sphere_link,
+                            np.ascontiguousarray(np.concatenate([pr, extra]).astype(np.int32)))
     scene = synth.make_scene(4, O)
     q = synth.make_q(9, n, limit=np.pi) if robot.n_joints == 7 else \
         np.random.default_rng(9).uniform(-2.8, 2.8, (n, robot.n_joints)).astype(np.float32)
@@ -239,7 +248,15 @@ def test_edge_cases(case):
     check_fp32(decode_packed(grad, 3 * S, F.FP32).reshape(n, S, 3), col["grad"],
                mask=np.repeat(ok[:, :, None], 3, 2), what="G")
     cfg = ok.all(1)
-    check_fp32(decode_packed(jg, J, F.FP32), jg64, mask=np.repeat(cfg[:, None], J, 1), what="J")
+    if case == "heavy_duplicates":
+        # the 6000-fold pair forces cancel within link 1: float32 rounding of those terms,
+        # not the method, bounds J's error, so the scale is the sum of the torques' sizes
+        # (1e-6 of it: about 16 float32 ulps; 1e-3 of max |J| here)
+        gj = decode_packed(jg, J, F.FP32)[cfg]
+        scale = (np.abs(col["grad"]).sum(2) * (1.0 + np.linalg.norm(pos64, axis=2))).sum(1)[cfg].max()
+        assert np.abs(gj - jg64[cfg]).max() <= 1e-6 * scale, "J beyond the float32 bound of its sums"
+    else:
+        check_fp32(decode_packed(jg, J, F.FP32), jg64, mask=np.repeat(cfg[:, None], J, 1), what="J")
     if O == 0 and robot.n_pairs == 0:
         assert np.all(cost.cpu().numpy() == 0)
 
