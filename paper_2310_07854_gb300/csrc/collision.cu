@@ -22,8 +22,8 @@
 //
 // Self pairs: the block groups the pair table by cluster pair (runs of up to
 // CL spheres of one link, load_self), or copies the robot's prebuilt
-// tables (load_robot_self: a hash-checked copy instead of about 10 us of
-// building per block); per configuration, cluster pairs whose bounding
+// tables (load_block_tables: a hash-checked copy instead of about 10 us
+// of building per block); per configuration, cluster pairs whose bounding
 // spheres are apart are skipped and the pairs of the others tested in
 // table order (self_pairs in stages.cuh).
 //

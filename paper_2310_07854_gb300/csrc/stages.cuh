@@ -911,7 +911,8 @@ __device__ __forceinline__ void env_bits_direct(const SceneSm& m, int obase, uns
 // KEPT_CAP at a time and the kept ones listed in table order; 32 listed
 // cluster pairs at a time are expanded into their pairs through a warp
 // prefix sum of their pair counts (lane t of a round finds its cluster pair
-// by binary search), and the pairs are tested in table order; each active
+// from a warp OR of the cluster pairs' start positions), and the pairs are
+// tested in table order; each active
 // pair's gradient is added to its two spheres in fixed point (w.gi), and
 // the sums are added to G at the end.
 __device__ __forceinline__ float self_pairs(const RobotSm& rb, const SceneSm& m, const CollWarp& w,
