@@ -122,8 +122,10 @@ typedef struct {
  * vapr_cost_grad, vapr_cost_grad_noalloc, vapr_cost_grad_fused, the
  * multi-problem launch) first lays out, in each block's shared memory, the
  * robot's spheres grouped by link, its self-collision clusters (runs of up
- * to 3 spheres of one link) and its self pairs grouped by cluster pair (the
- * self-collision broad phase of iteration step 3, Sec. III-B).  Building
+ * to 3 spheres of one link), its self pairs grouped by cluster pair (the
+ * self-collision broad phase of iteration step 3, Sec. III-B) and the
+ * fixed-point exponent of the self terms' sums (from the most pairs that
+ * name one sphere).  Building
  * that takes each block about 10 us for an arm with 832 pairs; with
  * robot->tables set, the blocks copy tables built once instead.  Each
  * launch checks on the device that the tables were built for the robot's
